@@ -1,0 +1,73 @@
+"""Write oracle fronts for full-size synthetic workloads as text fixtures.
+
+Usage: python tests/golden/make_golden.py config2 [--seed 1]
+       python tests/golden/make_golden.py config4 --seed 1 --queries 0:64
+
+Only the oracle (Algorithm 1, ``oracle/``) and the input generators
+(``synth``) are called. Each fixture records the graph digest so a test can
+tell whether the graph it regenerated is the one the front belongs to.
+
+File format (one fixture per query):
+    # <free text>
+    graph <name> <digest>
+    query <start> <goal>
+    d <d>
+    stats <key>=<value> ...
+    count <k>
+    <c_0> <c_1> ... <c_{d-1}>      (k lines, lexicographic order)
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+_ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, _ROOT)
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def write_front(path, g, s, t, front, note=""):
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        f.write(f"# oracle front (Algorithm 1, sequential NAMOA*) {note}\n")
+        f.write(f"graph {g.name} {g.digest()}\n")
+        f.write(f"query {s} {t}\n")
+        f.write(f"d {g.d}\n")
+        f.write("stats " + " ".join(f"{k}={v}" for k, v in front.stats.items()) + "\n")
+        f.write(f"count {len(front.costs)}\n")
+        for row in front.costs:
+            f.write(" ".join(str(int(x)) for x in row) + "\n")
+    os.replace(tmp, path)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("config", choices=["config1", "config2", "config3", "config4"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--queries", default="0:1", help="slice lo:hi of the config's query list")
+    ap.add_argument("--d", type=int, default=0, help="use only the first d objectives")
+    args = ap.parse_args()
+    g, queries = getattr(synth, args.config)(args.seed)
+    if args.d:
+        g = g.first_objectives(args.d)
+    lo, hi = (int(x) for x in args.queries.split(":"))
+    for qi in range(lo, min(hi, len(queries))):
+        s, t = queries[qi]
+        t0 = time.time()
+        front = oracle.solve(g, s, t)
+        dt = time.time() - t0
+        suffix = f"_d{args.d}" if args.d else ""
+        path = os.path.join(HERE, f"{args.config}_seed{args.seed}{suffix}_q{qi}.front")
+        write_front(path, g, s, t, front, note=f"wall {dt:.1f}s")
+        print(f"{path}: {len(front.costs)} solutions, {front.stats['labels']} labels, {dt:.1f}s",
+              flush=True)
+
+
+if __name__ == "__main__":
+    main()
