@@ -1,7 +1,7 @@
 """Write oracle fronts for full-size synthetic workloads as text fixtures.
 
 Usage: python tests/golden/make_golden.py config2 [--seed 1]
-       python tests/golden/make_golden.py config4 --seed 1 --queries 0:64
+       python tests/golden/make_golden.py config4 --digests --jobs 6
 
 Only the oracle (Algorithm 1, ``oracle/``) and the input generators
 (``synth``) are called. Each fixture records the graph digest so a test can
@@ -15,10 +15,18 @@ File format (one fixture per query):
     stats <key>=<value> ...
     count <k>
     <c_0> <c_1> ... <c_{d-1}>      (k lines, lexicographic order)
+
+Digest format (``--digests``; one line per query of the config):
+    <qi> <start> <goal> <count> <labels> <extracted> <sha256 of the sorted
+    front as little-endian uint32, first 16 hex digits>
+A query the oracle cannot finish within ``--budget`` labels is written with
+count -1.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
+import multiprocessing as mp
 import os
 import sys
 import time
@@ -46,13 +54,60 @@ def write_front(path, g, s, t, front, note=""):
     os.replace(tmp, path)
 
 
+def front_digest(costs) -> str:
+    import numpy as np
+    return hashlib.sha256(np.ascontiguousarray(costs, dtype="<u4").tobytes()).hexdigest()[:16]
+
+
+def _digest_job(args):
+    config, seed, d, budget, qi = args
+    g, queries = getattr(synth, config)(seed)
+    if d:
+        g = g.first_objectives(d)
+    s, t = queries[qi]
+    try:
+        f = oracle.solve(g, s, t, label_budget=budget)
+    except oracle.OracleError as e:
+        if e.code != oracle.BUDGET:
+            raise
+        return f"{qi} {s} {t} -1 -1 -1 -"
+    return (f"{qi} {s} {t} {len(f.costs)} {f.stats['labels']} {f.stats['extracted']} "
+            f"{front_digest(f.costs)}")
+
+
+def write_digests(args):
+    g, queries = getattr(synth, args.config)(args.seed)
+    if args.d:
+        g = g.first_objectives(args.d)
+    jobs = [(args.config, args.seed, args.d, args.budget, qi) for qi in range(len(queries))]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(args.jobs) as pool:
+        lines = pool.map(_digest_job, jobs, chunksize=4)
+    suffix = f"_d{args.d}" if args.d else ""
+    path = os.path.join(HERE, f"{args.config}_seed{args.seed}{suffix}.digests")
+    with open(path + ".tmp", "w") as f:
+        f.write(f"# oracle fronts (Algorithm 1) as digests; label budget {args.budget or 'none'}\n")
+        f.write(f"graph {g.name} {g.digest()}\n")
+        f.write("# qi start goal count labels extracted sha256[:16]\n")
+        for line in lines:
+            f.write(line + "\n")
+    os.replace(path + ".tmp", path)
+    print(path, len(lines), "queries")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("config", choices=["config1", "config2", "config3", "config4"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--queries", default="0:1", help="slice lo:hi of the config's query list")
     ap.add_argument("--d", type=int, default=0, help="use only the first d objectives")
+    ap.add_argument("--digests", action="store_true", help="all queries, digest lines")
+    ap.add_argument("--jobs", type=int, default=4)
+    ap.add_argument("--budget", type=int, default=0, help="oracle label budget per query")
     args = ap.parse_args()
+    if args.digests:
+        write_digests(args)
+        return
     g, queries = getattr(synth, args.config)(args.seed)
     if args.d:
         g = g.first_objectives(args.d)
