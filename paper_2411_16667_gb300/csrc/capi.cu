@@ -1,0 +1,752 @@
+// C ABI (include/opmos.h): argument checking, device memory, launches and
+// result marshalling. Every step of the search runs in the kernels of
+// search.cu and heuristic.cu; this file only moves data and sizes arenas.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "opmos.h"
+#include "search.cuh"
+
+using namespace opmos;
+
+namespace {
+
+thread_local std::string g_err;
+std::mutex g_mu;  // the library runs one call at a time per process
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(OPMOS_ERR_OUT_OF_MEMORY, "%s: %s", what, cudaGetErrorString(e));
+  }
+  return fail(OPMOS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                       \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+struct DevInfo {
+  bool ok = false;
+  int sms = 0;
+  int dev = 0;
+};
+
+DevInfo device_info() {
+  DevInfo di;
+  int cnt = 0;
+  if (cudaGetDeviceCount(&cnt) != cudaSuccess || cnt == 0) {
+    cudaGetLastError();
+    return di;
+  }
+  cudaGetDevice(&di.dev);
+  cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, di.dev);
+  di.ok = di.sms > 0;
+  return di;
+}
+
+// A grow-only device buffer reused across calls.
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int get(size_t want, void** out) {
+    if (want > bytes) {
+      if (ptr) cudaFree(ptr);
+      ptr = nullptr;
+      bytes = 0;
+      cudaError_t e = cudaMalloc(&ptr, want);
+      if (e != cudaSuccess) {
+        ptr = nullptr;
+        return cuda_fail(e, "cudaMalloc(workspace)");
+      }
+      bytes = want;
+    }
+    *out = ptr;
+    return OPMOS_OK;
+  }
+};
+
+Workspace g_arena, g_out, g_scratch, g_misc;
+
+template <class T>
+T* carve(char*& p, size_t count, size_t align = 256) {
+  uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  a = (a + align - 1) / align * align;
+  T* r = reinterpret_cast<T*>(a);
+  p = reinterpret_cast<char*>(a + count * sizeof(T));
+  return r;
+}
+
+}  // namespace
+
+struct opmos_graph {
+  uint32_t n = 0, d = 0, maxdeg = 0;
+  uint64_t m = 0;
+  uint32_t *rowptr = nullptr, *col = nullptr, *cost = nullptr;
+  uint32_t *rrowptr = nullptr, *rsrc = nullptr, *rcost = nullptr;
+  uint32_t* delta = nullptr;  // per objective, device
+  GraphDev dev{};
+};
+
+struct opmos_heur {
+  const opmos_graph* g = nullptr;
+  uint32_t goal = 0, d = 0;
+  uint32_t* h = nullptr;
+  uint64_t ns = 0;
+};
+
+struct opmos_result {
+  uint32_t count = 0, d = 0;
+  bool has_paths = false;
+  std::vector<uint32_t> costs, offs, nodes;
+  std::vector<uint64_t> edges;
+  opmos_stats stats{};
+};
+
+namespace {
+
+void free_graph(opmos_graph* g) {
+  if (!g) return;
+  for (uint32_t* p : {g->rowptr, g->col, g->cost, g->rrowptr, g->rsrc, g->rcost, g->delta})
+    if (p) cudaFree(p);
+  delete g;
+}
+
+opmos_options resolve(const opmos_options* in, bool batch) {
+  opmos_options o;
+  opmos_default_options(&o);
+  if (batch) {
+    o.window = 256;
+    o.mem_budget_bytes = 24ull << 30;
+  }
+  if (!in) return o;
+  if (in->window) o.window = in->window;
+  if (in->lanes_per_label) o.lanes_per_label = in->lanes_per_label;
+  if (in->tile) o.tile = in->tile;
+  if (in->delta) o.delta = in->delta;
+  if (in->label_budget) o.label_budget = in->label_budget;
+  if (in->mem_budget_bytes) o.mem_budget_bytes = in->mem_budget_bytes;
+  if (in->d_used) o.d_used = in->d_used;
+  o.flags = in->flags;
+  o.stream = in->stream;
+  return o;
+}
+
+int check_options(const opmos_options& o, const opmos_graph* g, uint32_t* d_used) {
+  const uint32_t du = o.d_used ? o.d_used : g->d;
+  if (du < 1 || du > g->d) return fail(OPMOS_ERR_INVALID_ARG, "d_used %u not in [1, %u]", du, g->d);
+  if (o.lanes_per_label != 4 && o.lanes_per_label != 8 && o.lanes_per_label != 16 && o.lanes_per_label != 32)
+    return fail(OPMOS_ERR_INVALID_ARG, "lanes_per_label must be 4, 8, 16 or 32");
+  if (o.tile % 32 || o.tile == 0) return fail(OPMOS_ERR_INVALID_ARG, "tile must be a positive multiple of 32");
+  if (o.window == 0 || o.window > (1u << 22)) return fail(OPMOS_ERR_INVALID_ARG, "window out of range");
+  *d_used = du;
+  return OPMOS_OK;
+}
+
+// Sizes of one query arena for a given byte budget.
+struct ArenaPlan {
+  uint32_t label_cap, open_cap, win_cap, cand_cap, plog_cap;
+  unsigned long long fpool_words;
+  size_t bytes;
+};
+
+int plan_arena(const opmos_graph* g, uint32_t D, uint32_t window, size_t budget, bool batch, ArenaPlan* pl) {
+  const size_t n = g->n;
+  pl->win_cap = 4 * window;
+  pl->cand_cap = pl->win_cap * std::max<uint32_t>(g->maxdeg, 1);
+  pl->plog_cap = batch ? (1u << 16) : (1u << 20);
+  size_t fixed = n * (8 + 4 + 4 + 4) + 2 * kNB * 4 + (size_t)pl->win_cap * 4 +
+                 (size_t)pl->cand_cap * (16 + 4 * D + 4) + (size_t)pl->plog_cap * 4 * D + 64 * 256;
+  if (budget < fixed + (8u << 20))
+    return fail(OPMOS_ERR_CAPACITY, "arena budget %zu too small (fixed part %zu)", budget, fixed);
+  const size_t rem = budget - fixed;
+  const size_t per_label = 4 * D + 17;
+  size_t labels = rem * 30 / 100 / per_label;
+  labels = std::min<size_t>(labels, 0xFFFFFF00u);
+  pl->label_cap = (uint32_t)labels;
+  pl->fpool_words = rem * 55 / 100 / 4;
+  size_t open = rem * 15 / 100 / 16;
+  pl->open_cap = (uint32_t)std::min<size_t>(open, 0xFFFFFF00u);
+  pl->bytes = budget;
+  return OPMOS_OK;
+}
+
+void layout_arena(const opmos_graph* g, uint32_t D, const ArenaPlan& pl, char* base, QArena* A) {
+  char* p = base;
+  const size_t n = g->n;
+  A->fbase = carve<uint64_t>(p, n);
+  A->fcount = carve<uint32_t>(p, n);
+  A->fcap = carve<uint32_t>(p, n);
+  A->node_head = carve<int32_t>(p, n);
+  A->hist = carve<uint32_t>(p, 2 * kNB);
+  A->window = carve<uint32_t>(p, pl.win_cap);
+  A->cnode = carve<uint32_t>(p, pl.cand_cap);
+  A->cparent = carve<uint32_t>(p, pl.cand_cap);
+  A->cedge = carve<uint32_t>(p, pl.cand_cap);
+  A->cnext = carve<int32_t>(p, pl.cand_cap);
+  A->touched = carve<uint32_t>(p, pl.cand_cap);
+  A->cg = carve<uint32_t>(p, (size_t)pl.cand_cap * D);
+  A->plog = carve<uint32_t>(p, (size_t)pl.plog_cap * D);
+  A->lg = carve<uint32_t>(p, (size_t)pl.label_cap * D);
+  A->lnode = carve<uint32_t>(p, pl.label_cap);
+  A->lparent = carve<uint32_t>(p, pl.label_cap);
+  A->ledge = carve<uint32_t>(p, pl.label_cap);
+  A->lpver = carve<uint32_t>(p, pl.label_cap);
+  A->lstatus = carve<uint8_t>(p, pl.label_cap);
+  A->open[0] = carve<uint64_t>(p, pl.open_cap);
+  A->open[1] = carve<uint64_t>(p, pl.open_cap);
+  A->fpool = carve<uint32_t>(p, pl.fpool_words);
+  A->label_cap = pl.label_cap;
+  A->open_cap = pl.open_cap;
+  A->win_cap = pl.win_cap;
+  A->cand_cap = pl.cand_cap;
+  A->plog_cap = pl.plog_cap;
+  A->fpool_words = pl.fpool_words;
+}
+
+int compute_heuristic(const opmos_graph* g, uint32_t D, const uint32_t* goals, uint32_t ngoals, uint32_t* h,
+                      cudaStream_t s, uint64_t* ns) {
+  const DevInfo di = device_info();
+  if (!di.ok) return fail(OPMOS_ERR_CUDA, "no CUDA device");
+  const unsigned njobs = ngoals * D;
+  std::vector<HJob> jobs(njobs);
+  for (uint32_t q = 0; q < ngoals; ++q)
+    for (uint32_t k = 0; k < D; ++k) jobs[q * D + k] = HJob{goals[q], k, h + ((size_t)q * D + k) * g->n};
+  const unsigned blocks = std::min<unsigned>(njobs, (unsigned)di.sms * 2);
+  const size_t spb = 5 * (size_t)g->n + 64;
+  void* scratch = nullptr;
+  if (int rc = g_scratch.get(spb * blocks * 4, &scratch)) return rc;
+  void* misc = nullptr;
+  const size_t jobs_bytes = njobs * sizeof(HJob);
+  if (int rc = g_misc.get(jobs_bytes + 1024, &misc)) return rc;
+  char* mp = (char*)misc;
+  unsigned* ctr = carve<unsigned>(mp, 2);
+  HJob* djobs = carve<HJob>(mp, njobs);
+  CK(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), s));
+  CK(cudaMemcpyAsync(djobs, jobs.data(), jobs_bytes, cudaMemcpyHostToDevice, s));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  cudaError_t e = launch_heuristic(g->dev, djobs, njobs, (uint32_t*)scratch, spb, blocks, g->delta, ctr,
+                                   ctr + 1, s);
+  cudaEventRecord(e1, s);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cuda_fail(e, "heuristic launch");
+  }
+  unsigned herr = 0;
+  cudaError_t e2 = cudaMemcpyAsync(&herr, ctr + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  cudaError_t e3 = cudaStreamSynchronize(s);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e2 != cudaSuccess) return cuda_fail(e2, "heuristic status copy");
+  if (e3 != cudaSuccess) return cuda_fail(e3, "heuristic kernel");
+  if (herr) return fail((int)herr, "heuristic kernel reported error %u", herr);
+  if (ns) *ns = (uint64_t)(ms * 1e6);
+  return OPMOS_OK;
+}
+
+void fill_stats(opmos_stats* s, const QResult& R, uint32_t D) {
+  s->extracted = R.stats[S_EXTRACTED];
+  s->dead_skipped = R.stats[S_DEAD];
+  s->goal_pruned = R.stats[S_GOALPRUNED];
+  s->candidates = R.stats[S_CAND];
+  s->inserted = R.stats[S_INSERTED];
+  s->pruned = R.stats[S_PRUNED];
+  s->steps = R.stats[S_STEPS];
+  s->frontier_cmp = R.stats[S_FCMP];
+  s->p_cmp = R.stats[S_PCMP];
+  // algorithmic bytes: per extracted label 8d+12 (g, node, rowptr pair, F key),
+  // per candidate 4+8d (col, cost, h), per compared frontier/P entry 4d, per
+  // inserted label 4d+24 (label record, frontier slot, OPEN entry), per prune 4.
+  const uint64_t d = D;
+  s->bytes = s->extracted * (8 * d + 12) + s->candidates * (4 + 8 * d) + (s->frontier_cmp + s->p_cmp) * 4 * d +
+             s->inserted * (4 * d + 24) + s->pruned * 4;
+}
+
+// Copy one query's output region to a host result.
+int take_result(const QResult& R, uint32_t D, bool paths, const uint32_t* words, cudaStream_t s,
+                opmos_result** out) {
+  auto* r = new (std::nothrow) opmos_result;
+  if (!r) return fail(OPMOS_ERR_OUT_OF_MEMORY, "host allocation");
+  r->count = R.count;
+  r->d = D;
+  r->has_paths = paths;
+  const size_t k = R.count;
+  r->costs.resize(k * D);
+  r->offs.resize(k + 1);
+  std::vector<uint32_t> tmp(k * D + k + 1);
+  if (!tmp.empty()) {
+    cudaError_t e = cudaMemcpyAsync(tmp.data(), words + R.off, tmp.size() * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) {
+      delete r;
+      return cuda_fail(e, "result copy");
+    }
+  }
+  std::vector<uint32_t> pw;
+  if (paths && R.total) {
+    pw.resize(2 * R.total - k);
+    cudaError_t e = cudaMemcpyAsync(pw.data(), words + R.path, pw.size() * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) {
+      delete r;
+      return cuda_fail(e, "path copy");
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    delete r;
+    return cuda_fail(e, "result copy");
+  }
+  std::copy(tmp.begin(), tmp.begin() + k * D, r->costs.begin());
+  std::copy(tmp.begin() + k * D, tmp.end(), r->offs.begin());
+  if (paths && R.total) {
+    r->nodes.assign(pw.begin(), pw.begin() + R.total);
+    r->edges.resize(R.total - k);
+    for (size_t i = 0; i < R.total - k; ++i) r->edges[i] = pw[R.total + i];
+  }
+  *out = r;
+  return OPMOS_OK;
+}
+
+int search_status(unsigned st) {
+  switch (st) {
+    case 0:
+      return OPMOS_OK;
+    case OPMOS_ERR_CAPACITY:
+      return fail(OPMOS_ERR_CAPACITY, "query arena full (labels, frontier pool, open list or output)");
+    case OPMOS_ERR_BUDGET:
+      return fail(OPMOS_ERR_BUDGET, "label budget exceeded");
+    case OPMOS_ERR_TIMEOUT:
+      return fail(OPMOS_ERR_TIMEOUT, "device-side wait or time limit expired");
+    default:
+      return fail((int)st, "search kernel error %u", st);
+  }
+}
+
+constexpr unsigned long long kTimeLimitNs = 300ull * 1000 * 1000 * 1000;
+constexpr size_t kOutWords = 64ull << 20;
+
+int solve_one(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint32_t goal, const opmos_options& o,
+              uint32_t D, opmos_result** out) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const DevInfo di = device_info();
+  if (!di.ok) return fail(OPMOS_ERR_CUDA, "no CUDA device");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  uint64_t hns = 0;
+  const uint32_t* h = nullptr;
+  opmos_heur tmp{};
+  if (heur) {
+    if (heur->g != g || heur->goal != goal || heur->d < D)
+      return fail(OPMOS_ERR_INVALID_ARG, "heuristic belongs to another graph, goal or objective count");
+    if (heur->d != D) return fail(OPMOS_ERR_INVALID_ARG, "heuristic computed for d=%u, query uses d=%u", heur->d, D);
+    h = heur->h;
+  } else {
+    CK(cudaMalloc(&tmp.h, (size_t)D * g->n * 4));
+    if (int rc = compute_heuristic(g, D, &goal, 1, tmp.h, s, &hns)) {
+      cudaFree(tmp.h);
+      return rc;
+    }
+    h = tmp.h;
+  }
+  struct Free {
+    uint32_t* p;
+    ~Free() {
+      if (p) cudaFree(p);
+    }
+  } free_h{tmp.h};
+
+  ArenaPlan pl;
+  if (int rc = plan_arena(g, D, o.window, o.mem_budget_bytes, false, &pl)) return rc;
+  void* arena = nullptr;
+  if (int rc = g_arena.get(pl.bytes, &arena)) return rc;
+  QArena A{};
+  layout_arena(g, D, pl, (char*)arena, &A);
+  void* outp = nullptr;
+  if (int rc = g_out.get(kOutWords * 4 + 1024, &outp)) return rc;
+  char* op = (char*)outp;
+  unsigned long long* used = carve<unsigned long long>(op, 1);
+  QCtl* C = carve<QCtl>(op, 1);
+  QResult* R = carve<QResult>(op, 1);
+  uint32_t* words = carve<uint32_t>(op, kOutWords);
+  OutPool O{words, kOutWords, used};
+  CK(cudaMemsetAsync(outp, 0, 1024, s));
+
+  QParams P{};
+  P.start = start;
+  P.goal = goal;
+  P.h = h;
+  P.window = o.window;
+  P.lanes = o.lanes_per_label;
+  P.delta = o.delta;
+  P.tile = o.tile;
+  P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, A.label_cap);
+  P.flags = o.flags;
+  P.time_limit_ns = kTimeLimitNs;
+
+  int occ = search_occupancy(D, 0);
+  if (occ <= 0) return fail(OPMOS_ERR_CUDA, "search kernel cannot be resident");
+  const unsigned blocks = (unsigned)di.sms * (unsigned)std::min(occ, 2);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  cudaError_t e = launch_search_grid(D, g->dev, A, C, P, O, R, blocks, s);
+  cudaEventRecord(e1, s);
+  QResult hr{};
+  cudaError_t e2 = e == cudaSuccess ? cudaMemcpyAsync(&hr, R, sizeof(QResult), cudaMemcpyDeviceToHost, s) : e;
+  cudaError_t e3 = cudaStreamSynchronize(s);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "search launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "search status copy");
+  if (e3 != cudaSuccess) return cuda_fail(e3, "search kernel");
+  if (int rc = search_status(hr.status)) return rc;
+  const bool paths = !(o.flags & OPMOS_FLAG_NO_PATHS);
+  opmos_result* r = nullptr;
+  if (int rc = take_result(hr, D, paths, words, s, &r)) return rc;
+  fill_stats(&r->stats, hr, D);
+  r->stats.heuristic_ns = heur ? 0 : hns;
+  r->stats.search_ns = (uint64_t)(ms * 1e6);
+  r->stats.total_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                          std::chrono::steady_clock::now() - t0).count();
+  *out = r;
+  return OPMOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void opmos_default_options(opmos_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->window = 4096;
+  o->lanes_per_label = 8;
+  o->tile = 32;
+  o->delta = 1;
+  o->label_budget = 0;
+  o->mem_budget_bytes = 8ull << 30;
+  o->d_used = 0;
+  o->flags = 0;
+  o->stream = nullptr;
+}
+
+int opmos_device_count(void) {
+  int c = 0;
+  if (cudaGetDeviceCount(&c) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return c;
+}
+
+const char* opmos_last_error(void) { return g_err.c_str(); }
+
+int opmos_graph_create(uint32_t n, uint64_t m, uint32_t d, const uint64_t* rowptr, const uint32_t* col,
+                       const uint32_t* cost, opmos_graph** out) {
+  if (!out) return fail(OPMOS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!rowptr || (m && (!col || !cost))) return fail(OPMOS_ERR_INVALID_ARG, "NULL array");
+  if (n == 0 || n >= (1u << 31)) return fail(OPMOS_ERR_INVALID_ARG, "n=%u out of range", n);
+  if (d < 1 || d > OPMOS_MAX_D) return fail(OPMOS_ERR_INVALID_ARG, "d=%u not in [1, %d]", d, OPMOS_MAX_D);
+  if (m >= 0xFFFFFFFFull) return fail(OPMOS_ERR_INVALID_ARG, "m too large");
+  if (rowptr[0] != 0 || rowptr[n] != m) return fail(OPMOS_ERR_INVALID_ARG, "rowptr[0] != 0 or rowptr[n] != m");
+  uint32_t maxdeg = 0;
+  for (uint32_t v = 0; v < n; ++v) {
+    if (rowptr[v + 1] < rowptr[v]) return fail(OPMOS_ERR_INVALID_ARG, "rowptr not monotone at %u", v);
+    maxdeg = std::max<uint32_t>(maxdeg, (uint32_t)(rowptr[v + 1] - rowptr[v]));
+  }
+  for (uint64_t e = 0; e < m; ++e)
+    if (col[e] >= n) return fail(OPMOS_ERR_INVALID_ARG, "col[%llu] = %u >= n", (unsigned long long)e, col[e]);
+  std::vector<uint32_t> delta(d);
+  for (uint32_t k = 0; k < d; ++k) {
+    uint64_t mx = 0, sum = 0;
+    for (uint64_t e = 0; e < m; ++e) {
+      mx = std::max<uint64_t>(mx, cost[k * m + e]);
+      sum += cost[k * m + e];
+    }
+    // g and F = g + h must fit uint32 on every simple path
+    if ((unsigned __int128)2 * (n - 1) * mx >= ((unsigned __int128)1 << 32))
+      return fail(OPMOS_ERR_OVERFLOW, "objective %u: 2*(n-1)*max cost does not fit uint32", k);
+    const uint64_t mean = m ? (sum + m - 1) / m : 1;
+    delta[k] = (uint32_t)std::max<uint64_t>(1, 2 * mean);
+  }
+  const DevInfo di = device_info();
+  if (!di.ok) return fail(OPMOS_ERR_CUDA, "no CUDA device");
+  // reversed CSR (in-arcs grouped by head node), costs carried along
+  std::vector<uint32_t> rp32(n + 1), rrp(n + 1, 0), rsrc(m), rcost((size_t)d * m);
+  for (uint32_t v = 0; v <= n; ++v) rp32[v] = (uint32_t)rowptr[v];
+  for (uint64_t e = 0; e < m; ++e) rrp[col[e] + 1]++;
+  for (uint32_t v = 0; v < n; ++v) rrp[v + 1] += rrp[v];
+  {
+    std::vector<uint32_t> fill(rrp.begin(), rrp.end() - 1);
+    for (uint32_t u = 0; u < n; ++u)
+      for (uint64_t e = rowptr[u]; e < rowptr[u + 1]; ++e) {
+        const uint32_t slot = fill[col[e]]++;
+        rsrc[slot] = u;
+        for (uint32_t k = 0; k < d; ++k) rcost[(size_t)k * m + slot] = cost[k * m + e];
+      }
+  }
+  auto* g = new (std::nothrow) opmos_graph;
+  if (!g) return fail(OPMOS_ERR_OUT_OF_MEMORY, "host allocation");
+  g->n = n;
+  g->m = m;
+  g->d = d;
+  g->maxdeg = maxdeg;
+  const size_t mb = std::max<size_t>(m, 1);
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](uint32_t** p, size_t words) {
+    if (e == cudaSuccess) e = cudaMalloc(p, words * 4);
+  };
+  alloc(&g->rowptr, n + 1);
+  alloc(&g->col, mb);
+  alloc(&g->cost, (size_t)d * mb);
+  alloc(&g->rrowptr, n + 1);
+  alloc(&g->rsrc, mb);
+  alloc(&g->rcost, (size_t)d * mb);
+  alloc(&g->delta, d);
+  if (e == cudaSuccess) e = cudaMemcpy(g->rowptr, rp32.data(), (n + 1) * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && m) e = cudaMemcpy(g->col, col, m * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && m) e = cudaMemcpy(g->cost, cost, (size_t)d * m * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->rrowptr, rrp.data(), (n + 1) * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && m) e = cudaMemcpy(g->rsrc, rsrc.data(), m * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && m) e = cudaMemcpy(g->rcost, rcost.data(), (size_t)d * m * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->delta, delta.data(), d * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_graph(g);
+    return cuda_fail(e, "graph upload");
+  }
+  g->dev = GraphDev{n, (uint32_t)m, d, maxdeg, g->rowptr, g->col, g->cost, g->rrowptr, g->rsrc, g->rcost};
+  *out = g;
+  return OPMOS_OK;
+}
+
+void opmos_graph_destroy(opmos_graph* g) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  free_graph(g);
+}
+
+int opmos_heuristic(const opmos_graph* g, uint32_t goal, uint32_t d_used, opmos_heur** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!out) return fail(OPMOS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!g) return fail(OPMOS_ERR_INVALID_ARG, "graph is NULL");
+  if (goal >= g->n) return fail(OPMOS_ERR_INVALID_ARG, "goal %u >= n", goal);
+  const uint32_t D = d_used ? d_used : g->d;
+  if (D > g->d) return fail(OPMOS_ERR_INVALID_ARG, "d_used %u > d %u", D, g->d);
+  auto* h = new (std::nothrow) opmos_heur;
+  if (!h) return fail(OPMOS_ERR_OUT_OF_MEMORY, "host allocation");
+  h->g = g;
+  h->goal = goal;
+  h->d = D;
+  cudaError_t e = cudaMalloc(&h->h, (size_t)D * g->n * 4);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "cudaMalloc(heuristic)");
+  }
+  if (int rc = compute_heuristic(g, D, &goal, 1, h->h, nullptr, &h->ns)) {
+    cudaFree(h->h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return OPMOS_OK;
+}
+
+int opmos_heuristic_copy(const opmos_heur* h, uint32_t* h_out) {
+  if (!h || !h_out) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+  cudaError_t e = cudaMemcpy(h_out, h->h, (size_t)h->d * h->g->n * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "heuristic copy");
+  return OPMOS_OK;
+}
+
+void opmos_heuristic_destroy(opmos_heur* h) {
+  if (!h) return;
+  if (h->h) cudaFree(h->h);
+  delete h;
+}
+
+int opmos_solve(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint32_t goal,
+                const opmos_options* opt, opmos_result** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!out) return fail(OPMOS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!g) return fail(OPMOS_ERR_INVALID_ARG, "graph is NULL");
+  if (start >= g->n || goal >= g->n) return fail(OPMOS_ERR_INVALID_ARG, "start/goal out of range");
+  const opmos_options o = resolve(opt, false);
+  uint32_t D;
+  if (int rc = check_options(o, g, &D)) return rc;
+  return solve_one(g, heur, start, goal, o, D, out);
+}
+
+int opmos_solve_batch(const opmos_graph* g, uint32_t nq, const uint32_t* starts, const uint32_t* goals,
+                      const opmos_options* opt, opmos_result** out, int* status) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g || !out || !status || (nq && (!starts || !goals))) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+  for (uint32_t q = 0; q < nq; ++q) {
+    out[q] = nullptr;
+    status[q] = OPMOS_ERR_INVALID_ARG;
+  }
+  for (uint32_t q = 0; q < nq; ++q)
+    if (starts[q] >= g->n || goals[q] >= g->n) return fail(OPMOS_ERR_INVALID_ARG, "query %u out of range", q);
+  const opmos_options o = resolve(opt, true);
+  uint32_t D;
+  if (int rc = check_options(o, g, &D)) return rc;
+  if (nq == 0) return OPMOS_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  const DevInfo di = device_info();
+  if (!di.ok) return fail(OPMOS_ERR_CUDA, "no CUDA device");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  // heuristics, one per distinct goal
+  std::map<uint32_t, uint32_t> gidx;
+  std::vector<uint32_t> ugoals;
+  for (uint32_t q = 0; q < nq; ++q)
+    if (gidx.emplace(goals[q], (uint32_t)ugoals.size()).second) ugoals.push_back(goals[q]);
+  uint32_t* hall = nullptr;
+  CK(cudaMalloc(&hall, (size_t)ugoals.size() * D * g->n * 4));
+  struct Free {
+    void* p;
+    ~Free() {
+      if (p) cudaFree(p);
+    }
+  } free_h{hall};
+  uint64_t hns = 0;
+  if (int rc = compute_heuristic(g, D, ugoals.data(), (uint32_t)ugoals.size(), hall, s, &hns)) return rc;
+  // slots: one thread block each, one arena each
+  int occ = search_occupancy(D, 1);
+  if (occ <= 0) return fail(OPMOS_ERR_CUDA, "batch kernel cannot be resident");
+  const unsigned slots = std::min<unsigned>(nq, (unsigned)di.sms * (unsigned)std::min(occ, 2));
+  ArenaPlan pl;
+  if (int rc = plan_arena(g, D, o.window, o.mem_budget_bytes / slots, true, &pl)) return rc;
+  const size_t slot_bytes = (pl.bytes + 255) / 256 * 256;
+  void* arena = nullptr;
+  if (int rc = g_arena.get(slot_bytes * slots, &arena)) return rc;
+  std::vector<QArena> arenas(slots);
+  for (unsigned i = 0; i < slots; ++i) layout_arena(g, D, pl, (char*)arena + i * slot_bytes, &arenas[i]);
+  std::vector<BatchQuery> qs(nq);
+  for (uint32_t q = 0; q < nq; ++q)
+    qs[q] = BatchQuery{starts[q], goals[q], hall + (size_t)gidx[goals[q]] * D * g->n};
+  const size_t out_words = std::max<size_t>(kOutWords, (size_t)nq * 4096);
+  void* outp = nullptr;
+  const size_t misc_bytes = slots * (sizeof(QArena) + sizeof(QCtl)) + nq * (sizeof(BatchQuery) + sizeof(QResult)) +
+                            8 * 256;
+  if (int rc = g_out.get(out_words * 4 + misc_bytes, &outp)) return rc;
+  char* op = (char*)outp;
+  unsigned long long* used = carve<unsigned long long>(op, 1);
+  unsigned* next_q = carve<unsigned>(op, 1);
+  QCtl* ctls = carve<QCtl>(op, slots);
+  QArena* darenas = carve<QArena>(op, slots);
+  BatchQuery* dqs = carve<BatchQuery>(op, nq);
+  QResult* dres = carve<QResult>(op, nq);
+  uint32_t* words = carve<uint32_t>(op, out_words);
+  CK(cudaMemsetAsync(used, 0, 8, s));
+  CK(cudaMemsetAsync(next_q, 0, 4, s));
+  CK(cudaMemsetAsync(ctls, 0, slots * sizeof(QCtl), s));
+  CK(cudaMemcpyAsync(darenas, arenas.data(), slots * sizeof(QArena), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dqs, qs.data(), nq * sizeof(BatchQuery), cudaMemcpyHostToDevice, s));
+  QParams P{};
+  P.window = o.window;
+  P.lanes = o.lanes_per_label;
+  P.delta = o.delta;
+  P.tile = o.tile;
+  P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, pl.label_cap);
+  P.flags = o.flags;
+  P.time_limit_ns = kTimeLimitNs;
+  OutPool O{words, out_words, used};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  cudaError_t e = launch_search_batch(D, g->dev, darenas, ctls, dqs, nq, next_q, P, O, dres, slots, s);
+  cudaEventRecord(e1, s);
+  std::vector<QResult> hres(nq);
+  cudaError_t e2 =
+      e == cudaSuccess ? cudaMemcpyAsync(hres.data(), dres, nq * sizeof(QResult), cudaMemcpyDeviceToHost, s) : e;
+  cudaError_t e3 = cudaStreamSynchronize(s);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "batch status copy");
+  if (e3 != cudaSuccess) return cuda_fail(e3, "batch kernel");
+  const bool paths = !(o.flags & OPMOS_FLAG_NO_PATHS);
+  const uint64_t total_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                std::chrono::steady_clock::now() - t0).count();
+  for (uint32_t q = 0; q < nq; ++q) {
+    const unsigned st = hres[q].status;
+    if (st != 0) {
+      status[q] = (int)st;
+      continue;
+    }
+    opmos_result* r = nullptr;
+    int rc = take_result(hres[q], D, paths, words, s, &r);
+    status[q] = rc;
+    if (rc) continue;
+    fill_stats(&r->stats, hres[q], D);
+    r->stats.heuristic_ns = hns;
+    r->stats.search_ns = (uint64_t)(ms * 1e6);
+    r->stats.total_ns = total_ns;
+    out[q] = r;
+  }
+  return OPMOS_OK;
+}
+
+uint32_t opmos_result_count(const opmos_result* r) { return r ? r->count : 0; }
+uint32_t opmos_result_d(const opmos_result* r) { return r ? r->d : 0; }
+
+int opmos_result_costs(const opmos_result* r, uint32_t* out) {
+  if (!r || (!out && r->count)) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+  if (r->count) std::memcpy(out, r->costs.data(), r->costs.size() * 4);
+  return OPMOS_OK;
+}
+
+int opmos_result_path(const opmos_result* r, uint32_t i, uint32_t* nodes, uint64_t* edges, uint32_t cap,
+                      uint32_t* len) {
+  if (!r || !len) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+  if (!r->has_paths) return fail(OPMOS_ERR_INVALID_ARG, "result was solved without paths");
+  if (i >= r->count) return fail(OPMOS_ERR_INVALID_ARG, "solution index %u >= count %u", i, r->count);
+  const uint32_t a = r->offs[i], b = r->offs[i + 1];
+  *len = b - a;
+  if (b - a > cap) return fail(OPMOS_ERR_CAPACITY, "path of %u nodes exceeds cap %u", b - a, cap);
+  if (!nodes || (b - a > 1 && !edges)) return fail(OPMOS_ERR_INVALID_ARG, "NULL output array");
+  std::memcpy(nodes, r->nodes.data() + a, (size_t)(b - a) * 4);
+  if (b - a > 1) std::memcpy(edges, r->edges.data() + (a - i), (size_t)(b - a - 1) * 8);
+  return OPMOS_OK;
+}
+
+int opmos_result_stats(const opmos_result* r, opmos_stats* out) {
+  if (!r || !out) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+  *out = r->stats;
+  return OPMOS_OK;
+}
+
+void opmos_result_free(opmos_result* r) { delete r; }
+
+}  // extern "C"

@@ -1,0 +1,44 @@
+// Host-visible declarations shared by the search kernels and the C ABI layer.
+#pragma once
+
+#include "opmos_dev.cuh"
+
+namespace opmos {
+
+struct BatchQuery {
+  uint32_t start, goal;
+  const uint32_t* h;  // d * n heuristic toward goal
+};
+
+// Result descriptor of one query, written by the team leader at the end.
+// Output words (in the OutPool): at off, count*d costs (lexicographic) then
+// count+1 path offsets; at path, total node ids then total-count arc ids.
+struct QResult {
+  unsigned status;
+  unsigned count;
+  unsigned long long off;
+  unsigned long long path;
+  unsigned long long total;
+  unsigned long long labels;
+  unsigned long long f_words;
+  unsigned long long stats[kNStat];
+};
+
+cudaError_t launch_search_grid(unsigned d, const GraphDev& G, const QArena& A, QCtl* C, const QParams& P,
+                               const OutPool& O, QResult* R, unsigned blocks, cudaStream_t s);
+cudaError_t launch_search_batch(unsigned d, const GraphDev& G, const QArena* arenas, QCtl* ctls,
+                                const BatchQuery* qs, unsigned nq, unsigned* next_q, const QParams& P,
+                                const OutPool& O, QResult* R, unsigned blocks, cudaStream_t s);
+int search_occupancy(unsigned d, int batch);
+
+// Ideal-point heuristic jobs: h_out[v] = shortest v->goal distance under
+// objective k (Sec. 4), one thread block per job.
+struct HJob {
+  uint32_t goal, k;
+  uint32_t* h_out;  // n entries
+};
+cudaError_t launch_heuristic(const GraphDev& G, const HJob* jobs, unsigned njobs, uint32_t* scratch,
+                             size_t scratch_words_per_block, unsigned blocks, const uint32_t* delta,
+                             unsigned* next_job, unsigned* err, cudaStream_t s);
+
+}  // namespace opmos

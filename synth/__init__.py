@@ -239,6 +239,22 @@ def config2(seed: int = 1) -> tuple[Graph, list[tuple[int, int]]]:
     return g, [(0, n - 1)]
 
 
+def ship_grid(seed: int, rows: int, d: int = 3) -> tuple[Graph, list[tuple[int, int]]]:
+    """A rows x rows version of the config-2 ship grid (same field recipe,
+    5% land, corner to corner), for test sizes; d <= 5 uses the config-4
+    objective list (length, time, fuel, exposure, steps)."""
+    sg = _ship_grid(seed, rows, rows)
+    n = rows * rows
+    src, dst = sg["src"], sg["dst"]
+    length = np.where(sg["diag"], 14, 10).astype(np.int64)
+    objs = [length, length * _edge_factor(sg["current"], src, dst), length * _edge_factor(sg["wave"], src, dst),
+            _edge_factor(sg["exposure"], src, dst), np.ones_like(length)]
+    cost = np.stack(objs[:d]).astype(np.uint32)
+    g = Graph(f"ship{rows}-d{d}-s{seed}", n, d, _rowptr(n, src), dst.astype(np.uint32), np.ascontiguousarray(cost),
+              {"rows": rows, "cols": rows, "seed": seed, "land_sub": sg["land_sub"]})
+    return g, [(0, n - 1)]
+
+
 def config4(seed: int = 1, nq: int = 1024) -> tuple[Graph, list[tuple[int, int]]]:
     """Config-2 grid plus obj4 = exposure factor in [1,8] and obj5 = 1 per move;
     ``nq`` queries with Chebyshev distance U[16,128] between reachable open cells."""

@@ -1,0 +1,55 @@
+"""CPU-side checks of the C ABI library: it builds, loads, exports every
+symbol include/opmos.h declares, and fails loudly without a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2411_16667_gb300 as pkg
+from paper_2411_16667_gb300 import opmos
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "opmos.h")).read()
+    return sorted(set(re.findall(r"OPMOS_API\s+[\w\s\*]+?\b(opmos_\w+)\(", text)))
+
+
+def test_header_declares_the_binding_exports():
+    assert _declared_symbols() == sorted(opmos.EXPORTS)
+
+
+def test_library_builds_and_exports_every_symbol():
+    path = pkg.build()
+    lib = ctypes.CDLL(path)
+    for name in _declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_options_struct_matches_defaults():
+    o = opmos.opmos_default_options()
+    assert (o.window, o.lanes_per_label, o.tile, o.delta) == (4096, 8, 32, 1)
+    assert o.mem_budget_bytes == 8 << 30
+    assert ctypes.sizeof(opmos.Options) == 48
+    assert ctypes.sizeof(opmos.Stats) == 13 * 8
+
+
+@pytest.mark.skipif(opmos.opmos_device_count() > 0, reason="only meaningful without a GPU")
+def test_no_device_fails_loudly():
+    import synth
+    g, _ = synth.config1()
+    with pytest.raises(opmos.OpmosError) as e:
+        opmos.opmos_graph.from_synth(g)
+    assert e.value.code == opmos.ERR_CUDA
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    saved = opmos._lib
+    try:
+        opmos._lib = None
+        with pytest.raises(opmos.OpmosError):
+            opmos.lib(str(tmp_path / "missing.so"))
+    finally:
+        opmos._lib = saved

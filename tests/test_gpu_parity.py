@@ -1,0 +1,249 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle.
+
+Fronts are compared bit-exactly as sets of uint32 cost vectors; every GPU
+path is re-verified (valid arcs, cost sum equals its vector). Paths are not
+compared with the oracle's, because several paths can carry the same cost.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from pins import check_front, load_front_fixture
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def op():
+    import paper_2411_16667_gb300 as pkg
+    pkg.build()
+    from paper_2411_16667_gb300 import opmos
+    if opmos.opmos_device_count() == 0:
+        pytest.fail("no CUDA device visible to the library")
+    return opmos
+
+
+def _same_front(res, expect: np.ndarray):
+    got = res.costs
+    assert got.shape == expect.shape, f"front size {got.shape[0]} != oracle {expect.shape[0]}"
+    assert np.array_equal(got, expect), "front differs from the oracle"
+
+
+# ---------------------------------------------------------------------------
+# heuristic (Sec. 4 ideal point) -- bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("maker", ["config1", "ship64", "rand"])
+def test_heuristic_matches_oracle(op, maker):
+    if maker == "config1":
+        g, q = synth.config1()
+    elif maker == "ship64":
+        g, q = synth.ship_grid(3, 64, 5)
+    else:
+        g = synth.random_digraph(11, 40, 3, p=0.08, cmax=9)
+        q = [(0, 7)]
+    goal = q[0][1]
+    G = op.opmos_graph.from_synth(g)
+    h = op.opmos_heur(G, goal).copy()
+    assert np.array_equal(h, oracle.heuristic(g, goal))
+
+
+def test_heuristic_full_size_ship_grid(op):
+    g, q = synth.config2()
+    G = op.opmos_graph.from_synth(g)
+    h = op.opmos_heur(G, q[0][1]).copy()
+    assert np.array_equal(h, oracle.heuristic(g, q[0][1]))
+
+
+# ---------------------------------------------------------------------------
+# single-query search -- bit-exact fronts
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(24))
+def test_random_digraphs(op, seed):
+    n = 5 + seed % 7
+    d = 1 + seed % 5
+    g = synth.random_digraph(seed, n, d, p=0.35, cmax=3)
+    s, t = 0, n - 1
+    exp = oracle.solve(g, s, t)
+    G = op.opmos_graph.from_synth(g)
+    res = op.opmos_solve(G, s, t, window=1 + seed % 5)
+    _same_front(res, exp.costs)
+    check_front(g, s, t, res.costs, res.paths)
+
+
+def test_config1_front(op):
+    g, q = synth.config1()
+    s, t = q[0]
+    exp = oracle.solve(g, s, t)
+    G = op.opmos_graph.from_synth(g)
+    res = op.opmos_solve(G, s, t)
+    _same_front(res, exp.costs)
+    check_front(g, s, t, res.costs, res.paths)
+    assert res.stats["extracted"] >= 1 and res.stats["steps"] >= 1
+
+
+@pytest.mark.parametrize("rows,d,seed", [(48, 3, 1), (64, 3, 2), (96, 3, 3), (64, 5, 4), (40, 2, 5), (33, 4, 6)])
+def test_ship_grids(op, rows, d, seed):
+    """Sizes span many frontier tiles with ragged tails and several windows."""
+    g, q = synth.ship_grid(seed, rows, d)
+    s, t = q[0]
+    exp = oracle.solve(g, s, t)
+    G = op.opmos_graph.from_synth(g)
+    res = op.opmos_solve(G, s, t)
+    _same_front(res, exp.costs)
+    check_front(g, s, t, res.costs, res.paths)
+
+
+@pytest.mark.parametrize("window,lanes,tile,delta", [(1, 4, 32, 1), (7, 16, 64, 1), (64, 32, 32, 3),
+                                                     (100000, 8, 128, 1), (512, 8, 32, 50)])
+def test_launch_parameters_do_not_change_the_front(op, window, lanes, tile, delta):
+    g, q = synth.ship_grid(7, 48, 3)
+    s, t = q[0]
+    exp = oracle.solve(g, s, t)
+    G = op.opmos_graph.from_synth(g)
+    res = op.opmos_solve(G, s, t, window=window, lanes_per_label=lanes, tile=tile, delta=delta)
+    _same_front(res, exp.costs)
+    check_front(g, s, t, res.costs, res.paths)
+
+
+def test_d_used_prefix_of_objectives(op):
+    g, q = synth.ship_grid(8, 48, 5)
+    s, t = q[0]
+    G = op.opmos_graph.from_synth(g)
+    for d in (1, 2, 4):
+        exp = oracle.solve(g.first_objectives(d), s, t)
+        res = op.opmos_solve(G, s, t, d_used=d)
+        _same_front(res, exp.costs)
+
+
+def test_given_heuristic_is_used(op):
+    g, q = synth.config1()
+    s, t = q[0]
+    G = op.opmos_graph.from_synth(g)
+    H = op.opmos_heur(G, t)
+    res = op.opmos_solve(G, s, t, heur=H)
+    _same_front(res, oracle.solve(g, s, t).costs)
+    assert res.stats["heuristic_ns"] == 0
+
+
+def test_config2_full_size_against_golden(op):
+    """Full 256x256 3-objective ship grid against the committed oracle front."""
+    meta, expect = load_front_fixture(os.path.join(GOLDEN, "config2_seed1_q0.front"))
+    g, q = synth.config2()
+    if g.digest() != meta["digest"]:
+        pytest.fail(f"regenerated graph digest {g.digest()} != fixture {meta['digest']}")
+    G = op.opmos_graph.from_synth(g)
+    res = op.opmos_solve(G, meta["start"], meta["goal"])
+    _same_front(res, expect)
+    check_front(g, meta["start"], meta["goal"], res.costs, res.paths)
+
+
+# ---------------------------------------------------------------------------
+# edge cases and errors
+# ---------------------------------------------------------------------------
+def test_start_equals_goal(op):
+    g = synth.small_grid(1, 4, 4, 3)
+    G = op.opmos_graph.from_synth(g)
+    res = op.opmos_solve(G, 5, 5)
+    assert res.costs.tolist() == [[0, 0, 0]]
+    assert res.paths[0][0].tolist() == [5] and res.paths[0][1].size == 0
+
+
+def test_unreachable_goal(op):
+    g = synth.from_arcs(3, [(0, 1, (1, 2)), (2, 1, (1, 1))])
+    G = op.opmos_graph.from_synth(g)
+    res = op.opmos_solve(G, 0, 2)
+    assert res.costs.shape == (0, 2)
+
+
+def test_zero_cost_cycles_and_ties(op):
+    g = synth.from_arcs(3, [(0, 1, (0, 0)), (1, 0, (0, 0)), (1, 2, (1, 0)), (0, 2, (0, 1))])
+    G = op.opmos_graph.from_synth(g)
+    res = op.opmos_solve(G, 0, 2)
+    assert res.costs.tolist() == [[0, 1], [1, 0]]
+    check_front(g, 0, 2, res.costs, res.paths)
+
+
+def test_no_paths_flag(op):
+    g, q = synth.config1()
+    G = op.opmos_graph.from_synth(g)
+    res = op.opmos_solve(G, *q[0], flags=op.FLAG_NO_PATHS)
+    assert res.paths is None
+    _same_front(res, oracle.solve(g, *q[0]).costs)
+
+
+def test_label_budget_is_reported(op):
+    g, q = synth.config1()
+    G = op.opmos_graph.from_synth(g)
+    with pytest.raises(op.OpmosError) as e:
+        op.opmos_solve(G, *q[0], label_budget=50)
+    assert e.value.code == op.ERR_BUDGET
+    # the library is usable afterwards
+    _same_front(op.opmos_solve(G, *q[0]), oracle.solve(g, *q[0]).costs)
+
+
+def test_small_arena_is_capacity_error(op):
+    g, q = synth.ship_grid(2, 96, 3)
+    G = op.opmos_graph.from_synth(g)
+    with pytest.raises(op.OpmosError) as e:
+        op.opmos_solve(G, *q[0], mem_budget_bytes=10 << 20, window=64)
+    assert e.value.code == op.ERR_CAPACITY
+
+
+def test_invalid_arguments(op):
+    g, q = synth.config1()
+    G = op.opmos_graph.from_synth(g)
+    for kw in ({"lanes_per_label": 3}, {"tile": 48}, {"d_used": 3}):
+        with pytest.raises(op.OpmosError) as e:
+            op.opmos_solve(G, *q[0], **kw)
+        assert e.value.code == op.ERR_INVALID_ARG
+    with pytest.raises(op.OpmosError) as e:
+        op.opmos_solve(G, 0, 5000)
+    assert e.value.code == op.ERR_INVALID_ARG
+    bad = synth.from_arcs(3, [(0, 1, (0xF0000000,)), (1, 2, (1,))])
+    with pytest.raises(op.OpmosError) as e:
+        op.opmos_graph.from_synth(bad)
+    assert e.value.code == op.ERR_OVERFLOW
+
+
+# ---------------------------------------------------------------------------
+# batch mode
+# ---------------------------------------------------------------------------
+def test_batch_matches_oracle_on_ship_queries(op):
+    g, queries = synth.config4(1, nq=48)
+    G = op.opmos_graph.from_synth(g)
+    starts = [s for s, _ in queries]
+    goals = [t for _, t in queries]
+    out = op.opmos_solve_batch(G, starts, goals)
+    for (s, t), (st, res) in zip(queries, out):
+        assert st == op.OK, f"query {s}->{t} status {st}"
+        exp = oracle.solve(g, s, t)
+        _same_front(res, exp.costs)
+        check_front(g, s, t, res.costs, res.paths)
+
+
+def test_batch_equals_single(op):
+    """Each query's front is the same alone and in the batch."""
+    g, queries = synth.config4(2, nq=12)
+    G = op.opmos_graph.from_synth(g)
+    out = op.opmos_solve_batch(G, [s for s, _ in queries], [t for _, t in queries], window=64)
+    for (s, t), (st, res) in zip(queries, out):
+        assert st == op.OK
+        alone = op.opmos_solve(G, s, t)
+        assert np.array_equal(res.costs, alone.costs)
+
+
+def test_batch_with_duplicate_and_trivial_queries(op):
+    g, q = synth.config1()
+    G = op.opmos_graph.from_synth(g)
+    s, t = q[0]
+    out = op.opmos_solve_batch(G, [s, s, t, 5], [t, t, t, 900])
+    exp = oracle.solve(g, s, t).costs
+    assert out[0][0] == op.OK and np.array_equal(out[0][1].costs, exp)
+    assert np.array_equal(out[1][1].costs, exp)
+    assert out[2][1].costs.tolist() == [[0, 0]]
+    _same_front(out[3][1], oracle.solve(g, 5, 900).costs)
