@@ -1,0 +1,269 @@
+#!/usr/bin/env python
+"""Benchmark of the exact multi-objective search on one GB300.
+
+Workload (default): one start->goal query on the seeded 256x256 8-connected
+3-objective ship grid (move length, length x current, length x wave; 5% land;
+corner to corner). A step is the whole hot path: ideal-point heuristic, the
+ordered-parallel search to the exact Pareto front, sorted front + paths, and
+the device->host copy of the result.
+
+value  = Pareto labels/s, counted as the oracle's number of labels extracted
+         for this query (taken from the committed oracle fixture) divided by
+         the GPU time-to-front, so labels the parallel search extracts beyond
+         the sequential count earn nothing. The GPU's own extraction rate and
+         the work ratio are reported beside it.
+e2e    = the same metric through the C ABI with host buffers: graph upload,
+         solve, result download, graph release inside the timed region.
+
+--impl reference times the oracle (sequential NAMOA*, Algorithm 1) on the host
+cores on a bounded sample of the same query (a label budget).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+FIXTURE = os.path.join(ROOT, "tests", "golden", "config2_seed1_q0.front")
+METRIC = "Pareto labels/s (time-to-front per query)"
+UNIT = "labels/s"
+CPU_SAMPLE_LABELS = 1_500_000
+
+
+def fixture_stats() -> dict:
+    """Oracle counters of the workload query, written by tests/golden/make_golden.py."""
+    meta = {}
+    with open(FIXTURE) as f:
+        for line in f:
+            if line.startswith("graph "):
+                meta["digest"] = line.split()[2]
+            elif line.startswith("stats "):
+                meta.update({k: int(v) for k, v in (kv.split("=") for kv in line.split()[1:])})
+            elif line.startswith("count "):
+                meta["count"] = int(line.split()[1])
+                break
+    return meta
+
+
+def cpu_sample(g, s, t, budget=CPU_SAMPLE_LABELS) -> dict:
+    """The oracle as it stands, single-threaded, on the first `budget` labels."""
+    import oracle
+    oracle.build()
+    h = oracle.heuristic(g, t)
+    res = oracle.solve(g, s, t, h=h, label_budget=budget, partial_ok=True)
+    st = res.stats
+    secs = st["ns"] / 1e9
+    return {"value": st["extracted"] / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"sequential NAMOA* (Algorithm 1) on the same query, stopped at {budget} labels "
+                      f"({st['extracted']} extracted in {secs:.2f} s main loop)"}
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    g, q = synth.config2()
+    s, t = q[0]
+    for _ in range(args.warmup):
+        cpu_sample(g, s, t, args.cpu_labels)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_sample(g, s, t, args.cpu_labels))
+    wall = time.perf_counter() - t0
+    v = statistics.median(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {**vals[-1], "value": v},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config():
+    return {"workload": "ship256-d3: 256x256 8-connected ship grid, 3 objectives (length, length x current, "
+                        "length x wave), 5% land, corner to corner, seed 1",
+            "queries_per_step": 1, "nodes": 65536, "objectives": 3,
+            "l2": "inputs and search state exceed L2; a 256 MiB buffer is also written between steps"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="opmos", choices=["opmos", "reference"])
+    ap.add_argument("--window", type=int, default=0)
+    ap.add_argument("--cpu-labels", type=int, default=CPU_SAMPLE_LABELS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import paper_2411_16667_gb300 as pkg
+    pkg.build()
+    from paper_2411_16667_gb300 import opmos
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    g, q = synth.config2()
+    s, t = q[0]
+    fx = fixture_stats()
+    if g.digest() != fx["digest"]:
+        raise RuntimeError("regenerated workload does not match the oracle fixture")
+    useful = fx["extracted"]
+    G = opmos.opmos_graph.from_synth(g)
+    opt = opmos.opmos_default_options(stream=stream.cuda_stream, window=args.window or None)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        return opmos.opmos_solve(G, s, t, options=opt)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            res = step()
+        if res.costs.shape[0] != fx["count"]:
+            raise RuntimeError(f"front size {res.costs.shape[0]} != oracle {fx['count']}")
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        stats = []
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                r = step()
+                ev[i][1].record(stream)
+                stats.append(r.stats)
+            torch.cuda.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        ms = sum(step_ms) / len(step_ms)
+        if world > 1:
+            tt = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+
+        # end to end through the C ABI with host buffers
+        h2d = g.rowptr.nbytes + g.col.nbytes + g.cost.nbytes
+        e2e_t, d2h = [], 0
+        for i in range(max(1, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Gh = opmos.opmos_graph.from_synth(g)
+            r = opmos.opmos_solve(Gh, s, t, options=opt)
+            Gh.close()
+            torch.cuda.synchronize()
+            e2e_t.append(time.perf_counter() - t0)
+            d2h = r.costs.nbytes + sum(a.nbytes // 2 + b.nbytes for a, b in r.paths)  # device words are u32
+
+    search_ns = statistics.median(x["search_ns"] for x in stats)
+    heur_ns = statistics.median(x["heuristic_ns"] for x in stats)
+    st = stats[-1]
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        peak, peak_src = 6800.0, "fallback"
+    achieved = st["bytes"] / (search_ns / 1e9) / 1e9
+    value = world * useful / (ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": workload_config(),
+        "time_to_front_ms": ms, "heuristic_ms": heur_ns / 1e6, "search_kernel_ms": search_ns / 1e6,
+        "gpu_labels_extracted": st["extracted"], "oracle_labels_extracted": useful,
+        "work_ratio": st["extracted"] / useful, "gpu_labels_per_s": st["extracted"] / (ms / 1e3),
+        "candidates_per_s": st["candidates"] / (ms / 1e3), "front_size": int(fx["count"]),
+        "search_steps": st["steps"], "step_ms_all": step_ms,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "search_grid_kernel",
+                     "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+                     else "fallback 6.8 TB/s"},
+        "e2e": {"value": world * useful / statistics.median(e2e_t), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_sample(g, s, t, args.cpu_labels)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -94,8 +94,11 @@ class Front:
     stats: dict
 
 
-def solve(g, start: int, goal: int, h: np.ndarray | None = None, label_budget: int = 0) -> Front:
-    """Exact Pareto front of start->goal by Algorithm 1."""
+def solve(g, start: int, goal: int, h: np.ndarray | None = None, label_budget: int = 0,
+          partial_ok: bool = False) -> Front:
+    """Exact Pareto front of start->goal by Algorithm 1. With ``partial_ok``
+    a run stopped by ``label_budget`` returns its counters (``stats['partial']
+    = 1``) and an empty front instead of raising."""
     lib = _load()
     rp, col, cost = _graph_arrays(g)
     hp = None
@@ -105,7 +108,10 @@ def solve(g, start: int, goal: int, h: np.ndarray | None = None, label_budget: i
     res = ctypes.c_void_p()
     rc = lib.oracle_solve(g.n, g.m, g.d, _ptr(rp), _ptr(col), _ptr(cost), hp, start, goal,
                           label_budget, ctypes.byref(res))
-    if rc:
+    partial = rc == BUDGET and bool(res.value)
+    if rc and not (partial and partial_ok):
+        if res.value:
+            lib.oracle_result_free(res)
         raise OracleError(rc, "solve")
     try:
         cnt = lib.oracle_result_count(res)
@@ -122,6 +128,7 @@ def solve(g, start: int, goal: int, h: np.ndarray | None = None, label_budget: i
         st = np.empty(len(STATS_FIELDS), np.uint64)
         lib.oracle_result_stats(res, _ptr(st))
         stats = {k: int(v) for k, v in zip(STATS_FIELDS, st)}
+        stats["partial"] = int(partial)
     finally:
         lib.oracle_result_free(res)
     return Front(costs, paths, stats)

@@ -208,9 +208,15 @@ struct Namoa {
     return true;
   }
 
+  std::chrono::steady_clock::time_point t0;
+
   int new_label(uint32_t v, uint32_t parent, uint64_t edge, const uint64_t* g, const uint64_t* F,
                 uint32_t* id) {
-    if (pool.size() >= budget) return ORC_BUDGET;
+    if (pool.size() >= budget) {
+      cnt.ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                   std::chrono::steady_clock::now() - t0).count();
+      return ORC_BUDGET;
+    }
     pool.node.push_back(v);
     pool.parent.push_back(parent);
     pool.edge.push_back(edge);
@@ -229,7 +235,7 @@ struct Namoa {
   }
 
   int run() {
-    auto t0 = std::chrono::steady_clock::now();
+    t0 = std::chrono::steady_clock::now();
     // lines 3-4: l_s = (v_s, 0), into OPEN and G_OP(v_s)
     uint64_t zero[kMaxD] = {0}, Fs[kMaxD];
     for (int i = 0; i < d; ++i) Fs[i] = h_inf(start) ? kInf64 : hv(i, start);
@@ -352,6 +358,8 @@ struct Namoa {
 
 struct oracle_result {
   uint32_t d = 0;
+  uint32_t partial = 0;                       // 1: stopped by the label budget
+  uint32_t partial_pad = 0;
   std::vector<uint32_t> costs;                // count*d, lexicographically sorted
   std::vector<std::vector<uint32_t>> nodes;   // per solution, start..goal
   std::vector<std::vector<uint64_t>> edges;   // per solution, arc ids
@@ -371,7 +379,9 @@ int oracle_heuristic(uint32_t n, uint64_t m, uint32_t d, const uint64_t* rowptr,
 }
 
 // Runs Algorithm 1. h may be NULL (computed here). label_budget = 0 means
-// unlimited. On success *out owns the front; on failure *out is NULL.
+// unlimited. On success *out owns the front. When the budget stops the run the
+// return code is ORC_BUDGET and *out holds the counters only (count 0); on any
+// other failure *out is NULL.
 int oracle_solve(uint32_t n, uint64_t m, uint32_t d, const uint64_t* rowptr, const uint32_t* col,
                  const uint32_t* cost, const uint32_t* h, uint32_t start, uint32_t goal,
                  uint64_t label_budget, oracle_result** out) {
@@ -387,11 +397,18 @@ int oracle_solve(uint32_t n, uint64_t m, uint32_t d, const uint64_t* rowptr, con
       h = hbuf.data();
     }
     Namoa S(G, h, start, goal, label_budget ? label_budget : ~0ull);
-    if (int rc = S.run()) return rc;
+    const int rc = S.run();
+    if (rc && rc != ORC_BUDGET) return rc;
     auto* r = new oracle_result;
     r->d = d;
     r->cnt = S.cnt;
     r->labels = S.pool.size();
+    if (rc == ORC_BUDGET) {
+      // stopped by the budget: counters only (the front is not final)
+      r->partial = 1;
+      *out = r;
+      return ORC_BUDGET;
+    }
     std::vector<uint32_t> P = S.P;
     std::sort(P.begin(), P.end(), [&](uint32_t a, uint32_t b) {
       for (uint32_t i = 0; i < d; ++i)

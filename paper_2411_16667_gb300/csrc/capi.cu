@@ -175,8 +175,10 @@ int plan_arena(const opmos_graph* g, uint32_t D, uint32_t window, size_t budget,
   pl->win_cap = 4 * window;
   pl->cand_cap = pl->win_cap * std::max<uint32_t>(g->maxdeg, 1);
   pl->plog_cap = batch ? (1u << 16) : (1u << 20);
+  const size_t ptiles = pl->plog_cap / 32 + 1;
   size_t fixed = n * (8 + 4 + 4 + 4) + 2 * kNB * 4 + (size_t)pl->win_cap * 4 +
-                 (size_t)pl->cand_cap * (16 + 4 * D + 4) + (size_t)pl->plog_cap * 4 * D + 64 * 256;
+                 (size_t)pl->cand_cap * (16 + 4 * D + 4) + (size_t)pl->plog_cap * 4 * D +
+                 2 * ((size_t)pl->plog_cap + ptiles) * 4 * D + 64 * 256;
   if (budget < fixed + (8u << 20))
     return fail(OPMOS_ERR_CAPACITY, "arena budget %zu too small (fixed part %zu)", budget, fixed);
   const size_t rem = budget - fixed;
@@ -185,7 +187,7 @@ int plan_arena(const opmos_graph* g, uint32_t D, uint32_t window, size_t budget,
   labels = std::min<size_t>(labels, 0xFFFFFF00u);
   pl->label_cap = (uint32_t)labels;
   pl->fpool_words = rem * 55 / 100 / 4;
-  size_t open = rem * 15 / 100 / 16;
+  size_t open = rem * 15 / 100 / 24;
   pl->open_cap = (uint32_t)std::min<size_t>(open, 0xFFFFFF00u);
   pl->bytes = budget;
   return OPMOS_OK;
@@ -213,8 +215,12 @@ void layout_arena(const opmos_graph* g, uint32_t D, const ArenaPlan& pl, char* b
   A->ledge = carve<uint32_t>(p, pl.label_cap);
   A->lpver = carve<uint32_t>(p, pl.label_cap);
   A->lstatus = carve<uint8_t>(p, pl.label_cap);
-  A->open[0] = carve<uint64_t>(p, pl.open_cap);
-  A->open[1] = carve<uint64_t>(p, pl.open_cap);
+  for (int b = 0; b < 2; ++b) {
+    A->okey[b] = carve<uint64_t>(p, pl.open_cap);
+    A->oid[b] = carve<uint32_t>(p, pl.open_cap);
+    A->ps[b] = carve<uint32_t>(p, (size_t)pl.plog_cap * D);
+    A->pst[b] = carve<uint32_t>(p, ((size_t)pl.plog_cap / 32 + 1) * D);
+  }
   A->fpool = carve<uint32_t>(p, pl.fpool_words);
   A->label_cap = pl.label_cap;
   A->open_cap = pl.open_cap;
@@ -699,8 +705,13 @@ int opmos_solve_batch(const opmos_graph* g, uint32_t nq, const uint32_t* starts,
   const bool paths = !(o.flags & OPMOS_FLAG_NO_PATHS);
   const uint64_t total_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
                                 std::chrono::steady_clock::now() - t0).count();
+  std::vector<uint32_t> retry;
   for (uint32_t q = 0; q < nq; ++q) {
     const unsigned st = hres[q].status;
+    if (st == OPMOS_ERR_CAPACITY) {
+      retry.push_back(q);  // outgrew its slot: re-run alone below
+      continue;
+    }
     if (st != 0) {
       status[q] = (int)st;
       continue;
@@ -714,6 +725,25 @@ int opmos_solve_batch(const opmos_graph* g, uint32_t nq, const uint32_t* starts,
     r->stats.search_ns = (uint64_t)(ms * 1e6);
     r->stats.total_ns = total_ns;
     out[q] = r;
+  }
+  // Queries whose front outgrew a batch slot run alone with a single-query
+  // arena (same options otherwise); their own status is reported.
+  if (!retry.empty()) {
+    opmos_options so = resolve(opt, false);
+    so.flags = o.flags;
+    so.stream = o.stream;
+    if (opt && opt->mem_budget_bytes) so.mem_budget_bytes = std::max<uint64_t>(opt->mem_budget_bytes / 2, 1ull << 30);
+    for (uint32_t q : retry) {
+      opmos_result* r = nullptr;
+      const size_t hoff = (size_t)gidx[goals[q]] * D * g->n;
+      opmos_heur hh{g, goals[q], D, hall + hoff, 0};
+      const int rc = solve_one(g, &hh, starts[q], goals[q], so, D, &r);
+      status[q] = rc;
+      if (rc == OPMOS_OK) {
+        r->stats.heuristic_ns = hns;
+        out[q] = r;
+      }
+    }
   }
   return OPMOS_OK;
 }

@@ -7,10 +7,13 @@
 //   frontier   per node v: a contiguous block at fpool[fbase[v]] of capacity
 //              fcap[v]: costs [k*cap + i] then label ids [d*cap + i]; fcount[v]
 //              live entries (alpha(v) = G_OP(v) u G_CL(v), Sec. 3)
-//   OPEN       two unsorted arrays of 64-bit entries (F[0] << 32 | label id),
-//              bucketed by F[0] through a per-step histogram (Algorithm 2 l.9-16)
+//   OPEN       two unsorted arrays of 64-bit keys (F[0] << 32 | F[1]) with
+//              label ids beside them, bucketed through a per-step histogram
+//              (Algorithm 2 l.9-16): the lowest F[0] bucket is split by F[1]
 //   P log      append-only list of every goal cost vector ever accepted; its
 //              prefix is a valid filter for "F dominated by P" (Alg. 1 l.19/29)
+//   P index    a snapshot of P sorted along a Z-order curve over objectives
+//              1..3, tiled by 32 with each tile's componentwise minimum
 #pragma once
 
 #include <cstdint>
@@ -22,7 +25,9 @@ namespace opmos {
 
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr int32_t kNil = -1;
-constexpr int kNB = 2048;  // open-list histogram buckets per step
+constexpr int kNB = 2048;   // open-list histogram buckets per step
+constexpr int kNB1 = 1024;  // of which sub-buckets (by F[1]) of the lowest F[0] bucket
+constexpr unsigned kPSMax = 32768;  // largest P indexed by the sorted snapshot
 
 enum : uint8_t { ST_OPEN = 0, ST_CLOSED = 1, ST_DEAD = 2 };
 
@@ -60,12 +65,17 @@ struct QCtl {
   unsigned win_count;
   unsigned cand_count;
   unsigned touched_count;
-  unsigned min_key[2];
   unsigned theta;
   unsigned plog_len;
   unsigned plog_snap;
   unsigned res_count;
   unsigned res_status;
+  unsigned f1span[2];     // F[1] spread of the lowest F[0] bucket, measured per step
+  unsigned ps_cur, ps_count, ps_mark, ps_ntiles;   // live P index
+  unsigned ps_build, ps_src, ps_mark_new, ps_nbuild;
+  unsigned ps_shift[3];
+  unsigned ps_nb;         // index buffer being built this step
+  unsigned long long min_key[2];  // lexicographic minimum (F0 << 32 | F1) of OPEN
   unsigned long long f_words;
   unsigned long long res_off;    // costs (count*d) then path offsets (count+1)
   unsigned long long res_path;   // nodes (total) then arc ids (total - count)
@@ -90,7 +100,10 @@ struct QArena {
   uint32_t* lpver;
   uint8_t* lstatus;
   uint32_t* fpool;
-  uint64_t* open[2];
+  uint64_t* okey[2];   // OPEN keys (F0 << 32 | F1)
+  uint32_t* oid[2];    // OPEN label ids
+  uint32_t* ps[2];     // P index: d * plog_cap costs, Z-order
+  uint32_t* pst[2];    // P index tile minima: d * (plog_cap / 32 + 1)
   uint32_t* window;
   uint32_t* cnode;
   uint32_t* cparent;
@@ -143,6 +156,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
   return *reinterpret_cast<const volatile unsigned*>(p);
+}
+__device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
 // Warp-aggregated atomic increment: one atomicAdd per group of converged lanes.

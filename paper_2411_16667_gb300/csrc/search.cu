@@ -3,8 +3,9 @@
 // grid for a single query, or one thread block per query in batch mode. A step
 // of the search is four phases separated by team barriers:
 //
-//   1. histogram   the open entries by bucket of F[0] (Algorithm 2 l.9, OPEN is
-//                  a lexicographic priority queue; F[0] is its first key)
+//   1. histogram   the open entries by lexicographic bucket of (F[0], F[1])
+//                  (Algorithm 2 l.9: OPEN is a lexicographic priority queue):
+//                  one bucket per F[0] value, the lowest one split by F[1]
 //   2. extract     the window = every live entry in the lowest buckets whose
 //                  cumulative count stays within W (the NUM_POP of Sec. 5);
 //                  entries whose label was pruned are dropped here (lazy OPEN
@@ -22,6 +23,12 @@
 //                  and OPEN. At the goal node alpha(v_g) is P itself (Alg. 1
 //                  l.11-13) and survivors are appended to the P log.
 //
+// The F-against-P test of phase 4 uses an index of P rebuilt every time P has
+// grown by about 1/8: P sorted along a Z-order curve over objectives 1..3 in
+// tiles of 32, each with its componentwise minimum; a candidate only scans the
+// tiles whose minimum weakly dominates it, plus the goal costs found since the
+// last rebuild (the rebuild is split over phases 1-3 of a step).
+//
 // A node is only ever touched by one warp per step, so frontier updates need
 // no locks. All waits are bounded (see GridTeam::sync).
 #include "opmos_dev.cuh"
@@ -32,6 +39,12 @@ namespace opmos {
 namespace {
 
 __device__ __forceinline__ unsigned warp_min(unsigned x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_min64(unsigned long long x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
   return x;
@@ -82,7 +95,44 @@ struct Shared {
   unsigned hist[kNB];
   unsigned warp[33];
   unsigned f_min, b1_max;
+  unsigned span;
+  unsigned pmax[3];
 };
+
+// Histogram bucket of an OPEN key (F0 << 32 | F1): buckets [0, kNB1) split the
+// lowest F0 bucket by F1 >> s1, buckets [kNB1, kNB-1) are whole F0 buckets of
+// width delta, kNB-1 collects everything beyond. Monotone in lexicographic
+// (F0, F1) order, so every prefix of buckets is a lexicographic prefix of OPEN.
+struct BinParams {
+  uint32_t b0, b1, s1, delta;
+};
+__device__ __forceinline__ unsigned bin_of(uint64_t key, const BinParams& bp) {
+  const uint32_t F0 = (uint32_t)(key >> 32), F1 = (uint32_t)key;
+  const uint32_t q = F0 > bp.b0 ? (F0 - bp.b0) / bp.delta : 0u;
+  if (q == 0) {
+    const uint32_t x = F1 > bp.b1 ? (F1 - bp.b1) >> bp.s1 : 0u;
+    return min(x, (unsigned)kNB1 - 1);
+  }
+  return kNB1 + min(q - 1, (unsigned)(kNB - kNB1 - 1));
+}
+
+// Z-order ("Morton") comparison without interleaving: the dimension whose
+// values differ in the highest bit decides.
+__device__ __forceinline__ bool msb_less(uint32_t a, uint32_t b) { return a < b && a < (a ^ b); }
+template <int MD>
+__device__ __forceinline__ bool z_less(const uint32_t (&a)[MD], const uint32_t (&b)[MD]) {
+  int dim = 0;
+  uint32_t x = 0;
+#pragma unroll
+  for (int k = 0; k < MD; ++k) {
+    const uint32_t y = a[k] ^ b[k];
+    if (msb_less(x, y)) {
+      dim = k;
+      x = y;
+    }
+  }
+  return a[dim] < b[dim];
+}
 
 template <int D>
 struct Search {
@@ -146,52 +196,164 @@ struct Search {
       C->f_words = (unsigned long long)(D + 1) * tile;
       C->n_labels = 1;
       C->plog_len = 0;
-      const uint32_t key = hk(0, s);
+      const uint32_t h0 = hk(0, s);
+      const uint64_t key = ((uint64_t)h0 << 32) | (D > 1 ? hk(1, s) : 0u);
       // start == goal: P = {l_s}, nothing to search. h(s) = inf: goal unreachable.
-      if (s != t && key != kInf) {
-        A.open[0][0] = ((uint64_t)key << 32) | 0u;
+      if (s != t && h0 != kInf) {
+        A.okey[0][0] = key;
+        A.oid[0][0] = 0;
         C->open_count[0] = 1;
         C->min_key[0] = key;
       } else {
         C->open_count[0] = 0;
-        C->min_key[0] = kInf;
+        C->min_key[0] = ~0ull;
       }
       C->open_count[1] = 0;
-      C->min_key[1] = kInf;
+      C->min_key[1] = ~0ull;
+      C->f1span[0] = C->f1span[1] = 0;
+      C->ps_cur = C->ps_count = C->ps_mark = C->ps_ntiles = 0;
+      C->ps_build = C->ps_src = C->ps_mark_new = C->ps_nbuild = C->ps_nb = 0;
       st[S_INSERTED] += 1;
     }
   }
 
   // ---------------- phase 1: bucket histogram of OPEN ----------------
   template <class Team>
-  __device__ void phase_hist(const Team& T, unsigned cur, unsigned n_in, unsigned base) {
+  __device__ void phase_hist(const Team& T, unsigned cur, unsigned n_in, const BinParams& bp) {
     for (unsigned i = threadIdx.x; i < kNB; i += blockDim.x) S.hist[i] = 0;
+    if (threadIdx.x == 0) S.span = 0;
     __syncthreads();
-    const uint64_t* in = A.open[cur];
-    const unsigned delta = P.delta;
+    const uint64_t* in = A.okey[cur];
+    unsigned span = 0;
     for (unsigned i = T.tid(); i < n_in; i += T.nthreads()) {
-      const unsigned key = (unsigned)(in[i] >> 32);
-      unsigned b = key <= base ? 0u : (key - base) / delta;
-      b = min(b, (unsigned)kNB - 1);
+      const uint64_t key = in[i];
+      const unsigned b = bin_of(key, bp);
       atomicAdd(&S.hist[b], 1u);
+      if (b < (unsigned)kNB1) span = max(span, (uint32_t)key - min((uint32_t)key, bp.b1));
     }
+    span = ~warp_min(~span);  // warp maximum
+    if (lane_id() == 0 && span) atomicMax(&S.span, span);
     __syncthreads();
     unsigned* gh = A.hist + cur * kNB;
     for (unsigned i = threadIdx.x; i < kNB; i += blockDim.x)
       if (S.hist[i]) atomicAdd(&gh[i], S.hist[i]);
+    const unsigned nxt = cur ^ 1u;
+    if (threadIdx.x == 0 && S.span) atomicMax(&C->f1span[nxt], S.span);
     if (T.leader()) {
-      const unsigned nxt = cur ^ 1u;
       C->open_count[nxt] = 0;
-      C->min_key[nxt] = kInf;
+      C->min_key[nxt] = ~0ull;
       C->win_count = 0;
       C->cand_count = 0;
       C->touched_count = 0;
     }
+    if (T.leader_block()) plan_p_index();
   }
 
-  // Threshold of the window: largest bucket b whose cumulative count is <= W,
-  // but at least the first non-empty bucket. Every block computes the same.
-  __device__ unsigned select_theta(unsigned cur, unsigned base) {
+  // Decide whether this step rebuilds the P index (P grew by ~1/8 since the
+  // last build) and fix the per-objective shifts that balance the Z-order.
+  __device__ void plan_p_index() {
+    if (D < 2) return;
+    const unsigned plen = ld_volatile(&C->plog_len);
+    const unsigned k = A.fcount[P.goal];
+    const bool build = plen - C->ps_mark > 32u + C->ps_count / 8u && k > 0 && k <= kPSMax;
+    if (threadIdx.x == 0) {
+      C->ps_build = build;
+      S.pmax[0] = S.pmax[1] = S.pmax[2] = 0;
+    }
+    if (!build) return;
+    __syncthreads();
+    constexpr int MD = D - 1 < 3 ? D - 1 : 3;
+    const uint64_t fb = A.fbase[P.goal];
+    const unsigned cap = A.fcap[P.goal];
+    unsigned mx[3] = {0, 0, 0};
+    for (unsigned i = threadIdx.x; i < k; i += blockDim.x)
+#pragma unroll
+      for (int j = 0; j < MD; ++j) mx[j] = max(mx[j], A.fpool[fb + (size_t)(j + 1) * cap + i] - hk(j + 1, P.start));
+#pragma unroll
+    for (int j = 0; j < MD; ++j) atomicMax(&S.pmax[j], mx[j]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int bl[3], mn = 32;
+#pragma unroll
+      for (int j = 0; j < MD; ++j) {
+        bl[j] = 32 - __clz(S.pmax[j]);
+        mn = min(mn, bl[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) C->ps_shift[j] = j < MD ? (unsigned)(bl[j] - mn) : 0u;
+      C->ps_src = k;
+      C->ps_mark_new = plen;
+      C->ps_nb = C->ps_cur ^ 1u;
+    }
+  }
+
+  // Phase 2 part of a rebuild: rank every P entry in Z-order and scatter it
+  // into the idle index buffer.
+  template <class Team>
+  __device__ void build_p_rank(const Team& T) {
+    if constexpr (D >= 2) {
+      constexpr int MD = D - 1 < 3 ? D - 1 : 3;
+      if (!ld_volatile(&C->ps_build)) return;
+      const unsigned k = C->ps_src;
+      const uint64_t fb = A.fbase[P.goal];
+      const unsigned cap = A.fcap[P.goal];
+      const unsigned nb = C->ps_nb;
+      uint32_t lo[MD], sh[MD];
+#pragma unroll
+      for (int j = 0; j < MD; ++j) {
+        lo[j] = hk(j + 1, P.start);
+        sh[j] = C->ps_shift[j];
+      }
+      for (unsigned i = T.tid(); i < k; i += T.nthreads()) {
+        uint32_t zi[MD];
+#pragma unroll
+        for (int j = 0; j < MD; ++j) zi[j] = (A.fpool[fb + (size_t)(j + 1) * cap + i] - lo[j]) >> sh[j];
+        unsigned rank = 0;
+        for (unsigned q = 0; q < k; ++q) {
+          uint32_t zq[MD];
+#pragma unroll
+          for (int j = 0; j < MD; ++j) zq[j] = (A.fpool[fb + (size_t)(j + 1) * cap + q] - lo[j]) >> sh[j];
+          rank += z_less<MD>(zq, zi) || (q < i && !z_less<MD>(zi, zq));
+        }
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) A.ps[nb][(size_t)kk * A.plog_cap + rank] = A.fpool[fb + (size_t)kk * cap + i];
+      }
+    }
+  }
+
+  // Phase 3 part of a rebuild: tile minima, then publish the new index.
+  template <class Team>
+  __device__ void build_p_tiles(const Team& T) {
+    if constexpr (D >= 2) {
+      if (!ld_volatile(&C->ps_build)) return;
+      const unsigned k = C->ps_src;
+      const unsigned nb = C->ps_nb;
+      const unsigned nt = (k + 31) / 32;
+      const size_t tcap = A.plog_cap / 32 + 1;
+      for (unsigned t = T.tid(); t < nt; t += T.nthreads()) {
+        uint32_t mn[D];
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) mn[kk] = kInf;
+        for (unsigned e = t * 32; e < min(k, t * 32 + 32); ++e)
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) mn[kk] = min(mn[kk], A.ps[nb][(size_t)kk * A.plog_cap + e]);
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) A.pst[nb][(size_t)kk * tcap + t] = mn[kk];
+      }
+      if (T.leader()) {
+        C->ps_cur = nb;
+        C->ps_count = k;
+        C->ps_ntiles = nt;
+        C->ps_mark = C->ps_mark_new;
+        C->ps_nbuild++;
+      }
+    }
+  }
+
+  // Window: buckets [0, b*] where b* is the largest bucket whose cumulative
+  // count is <= W, but at least the first non-empty bucket (the overflow bucket
+  // is never taken). Every block computes the same b*.
+  __device__ unsigned select_bucket(unsigned cur) {
     const unsigned* gh = A.hist + cur * kNB;
     const unsigned per = kNB / blockDim.x;  // blockDim divides kNB
     const unsigned b0 = threadIdx.x * per;
@@ -223,28 +385,28 @@ struct Search {
     if (fmin < kNB) atomicMin(&S.f_min, fmin);
     if (any_b1) atomicMax(&S.b1_max, b1);
     __syncthreads();
-    unsigned bstar = max(S.b1_max, S.f_min == (unsigned)kNB ? 0u : S.f_min);
+    const unsigned bstar = max(S.b1_max, S.f_min == (unsigned)kNB ? 0u : S.f_min);
     __syncthreads();
-    const unsigned long long th = (unsigned long long)base + (unsigned long long)(bstar + 1) * P.delta - 1;
-    return th >= kInf ? kInf - 1 : (unsigned)th;
+    return bstar;
   }
 
   // ---------------- phase 2: extraction (Algorithm 2 l.9-16) ----------------
   template <class Team>
-  __device__ void phase_extract(const Team& T, unsigned cur, unsigned n_in, unsigned base) {
-    const unsigned theta = select_theta(cur, base);
-    if (T.leader()) C->theta = theta;
+  __device__ void phase_extract(const Team& T, unsigned cur, unsigned n_in, const BinParams& bp) {
+    const unsigned bstar = select_bucket(cur);
+    if (T.leader()) C->theta = bstar;
     const unsigned nxt = cur ^ 1u;
-    const uint64_t* in = A.open[cur];
-    uint64_t* out = A.open[nxt];
+    const uint64_t* in = A.okey[cur];
+    const uint32_t* in_id = A.oid[cur];
+    uint64_t* out = A.okey[nxt];
+    uint32_t* out_id = A.oid[nxt];
     const unsigned plen = *reinterpret_cast<const volatile unsigned*>(&C->plog_len);
-    unsigned kmin = kInf;
+    unsigned long long kmin = ~0ull;
     for (unsigned i = T.tid(); i < n_in; i += T.nthreads()) {
-      const uint64_t e = in[i];
-      const unsigned key = (unsigned)(e >> 32);
-      const unsigned id = (unsigned)e;
+      const uint64_t key = in[i];
+      const unsigned id = in_id[i];
       bool keep = true;
-      if (key <= theta) {
+      if (bin_of(key, bp) <= bstar) {
         keep = false;
         const uint8_t s = A.lstatus[id];
         if (s == ST_DEAD) {
@@ -280,15 +442,17 @@ struct Search {
       if (keep) {
         const unsigned o = agg_inc(&C->open_count[nxt]);
         if (o < A.open_cap) {
-          out[o] = e;
-          kmin = min(kmin, key);
+          out[o] = key;
+          out_id[o] = id;
+          kmin = min(kmin, (unsigned long long)key);
         } else {
           set_error(C, OPMOS_ERR_CAPACITY);
         }
       }
     }
-    kmin = warp_min(kmin);
-    if (lane_id() == 0 && kmin != kInf) atomicMin(&C->min_key[nxt], kmin);
+    kmin = warp_min64(kmin);
+    if (lane_id() == 0 && kmin != ~0ull) atomicMin(&C->min_key[nxt], kmin);
+    build_p_rank(T);
   }
 
   // ---------------- phase 3: expansion (Algorithm 1 l.15-17) ----------------
@@ -296,7 +460,11 @@ struct Search {
   __device__ void phase_expand(const Team& T, unsigned nxt) {
     // the histogram of the next step starts from zero
     for (unsigned i = T.tid(); i < kNB; i += T.nthreads()) A.hist[nxt * kNB + i] = 0;
-    if (T.leader()) C->plog_snap = *reinterpret_cast<const volatile unsigned*>(&C->plog_len);
+    if (T.leader()) {
+      C->plog_snap = *reinterpret_cast<const volatile unsigned*>(&C->plog_len);
+      C->f1span[nxt ^ 1u] = 0;  // measured again by the next step's phase 1
+    }
+    build_p_tiles(T);
     const unsigned nw = min(*reinterpret_cast<const volatile unsigned*>(&C->win_count), A.win_cap);
     const unsigned L = P.lanes;
     const unsigned gl = T.tid() % L;
@@ -327,7 +495,8 @@ struct Search {
   }
 
   // ---------------- phase 4: merge (Algorithm 1 l.18-31, l.8-13) ----------------
-  __device__ void merge_batch(uint32_t v, int mine, unsigned nb, unsigned cur, unsigned psnap) {
+  __device__ void merge_batch(uint32_t v, int mine, unsigned nb, unsigned cur, unsigned psnap, unsigned pmark,
+                              unsigned pcount, unsigned pntiles, unsigned pbuf) {
     const unsigned lane = lane_id();
     const unsigned nxt = cur ^ 1u;
     const bool is_goal = (v == P.goal);
@@ -393,13 +562,15 @@ struct Search {
       __syncwarp();
       out += __popc(km);
     }
-    // (c) F against P (Algorithm 1 l.29); at the goal alpha(v_g) is P already
+    // (c) F against P (Algorithm 1 l.29); at the goal alpha(v_g) is P already.
+    // Recent goal costs are scanned directly, the rest through the P index.
     unsigned long long pcmp = 0;
     if (!is_goal && __any_sync(0xffffffffu, alive)) {
       uint32_t F[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) F[k] = c[k] + (valid ? hk(k, v) : 0u);
-      for (unsigned j0 = 0; j0 < psnap; j0 += 32) {
+      const unsigned t0 = pcount ? pmark : 0u;  // no index: scan the whole log
+      for (unsigned j0 = t0; j0 < psnap; j0 += 32) {
         unsigned amask = __ballot_sync(0xffffffffu, alive);
         if (!amask) break;
         const unsigned jj = j0 + lane;
@@ -416,6 +587,42 @@ struct Search {
           for (int k = 0; k < D; ++k) Fj[k] = __shfl_sync(0xffffffffu, F[k], j);
           const bool wd = vp && weakly_le<D>(p, Fj);
           if (__ballot_sync(0xffffffffu, wd) && lane == j) alive = false;
+        }
+      }
+      if (pcount) {
+        const uint32_t* ps = A.ps[pbuf];
+        const uint32_t* pst = A.pst[pbuf];
+        const size_t tcap = A.plog_cap / 32 + 1;
+        for (unsigned tg = 0; tg < pntiles; tg += 32) {
+          unsigned amask = __ballot_sync(0xffffffffu, alive);
+          if (!amask) break;
+          const unsigned tl = tg + lane;
+          const bool vt = tl < pntiles;
+          uint32_t tm[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) tm[k] = vt ? pst[(size_t)k * tcap + tl] : kInf;
+          while (amask) {
+            const unsigned j = __ffs(amask) - 1;
+            amask &= amask - 1;
+            uint32_t Fj[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) Fj[k] = __shfl_sync(0xffffffffu, F[k], j);
+            unsigned pm = __ballot_sync(0xffffffffu, vt && weakly_le<D>(tm, Fj));
+            pcmp += min(32u, pntiles - tg);
+            bool dead = false;
+            while (pm && !dead) {
+              const unsigned tt = __ffs(pm) - 1;
+              pm &= pm - 1;
+              const unsigned e = (tg + tt) * 32 + lane;
+              const bool ve = e < pcount;
+              uint32_t p[D];
+#pragma unroll
+              for (int k = 0; k < D; ++k) p[k] = ve ? ps[(size_t)k * A.plog_cap + e] : kInf;
+              dead = __ballot_sync(0xffffffffu, ve && weakly_le<D>(p, Fj)) != 0;
+              pcmp += 32;
+            }
+            if (dead && lane == j) alive = false;
+          }
         }
       }
     }
@@ -462,7 +669,7 @@ struct Search {
             return;
           }
         }
-        unsigned my_key = kInf;
+        unsigned long long my_key = ~0ull;
         if (alive) {
           const unsigned r = __popc(smask & lanemask_lt());
           const unsigned id = lb + r;
@@ -480,18 +687,19 @@ struct Search {
 #pragma unroll
             for (int k = 0; k < D; ++k) A.plog[(size_t)k * A.plog_cap + plen + r] = c[k];
           } else {
-            const uint32_t key = c[0] + hk(0, v);
+            const uint64_t key = ((uint64_t)(c[0] + hk(0, v)) << 32) | (D > 1 ? c[1 % D] + hk(1 % D, v) : 0u);
             const unsigned o = agg_inc(&C->open_count[nxt]);
             if (o < A.open_cap) {
-              A.open[nxt][o] = ((uint64_t)key << 32) | id;
+              A.okey[nxt][o] = key;
+              A.oid[nxt][o] = id;
               my_key = key;
             } else {
               set_error(C, OPMOS_ERR_CAPACITY);
             }
           }
         }
-        my_key = warp_min(my_key);
-        if (lane == 0 && my_key != kInf) atomicMin(&C->min_key[nxt], my_key);
+        my_key = warp_min64(my_key);
+        if (lane == 0 && my_key != ~0ull) atomicMin(&C->min_key[nxt], my_key);
         if (is_goal && lane == 0) {
           __threadfence();
           *reinterpret_cast<volatile unsigned*>(&C->plog_len) = plen + ns;
@@ -512,6 +720,10 @@ struct Search {
   __device__ void phase_merge(const Team& T, unsigned cur) {
     const unsigned nt = *reinterpret_cast<const volatile unsigned*>(&C->touched_count);
     const unsigned psnap = *reinterpret_cast<const volatile unsigned*>(&C->plog_snap);
+    const unsigned pcount = ld_volatile(&C->ps_count);
+    const unsigned pmark = ld_volatile(&C->ps_mark);
+    const unsigned pntiles = ld_volatile(&C->ps_ntiles);
+    const unsigned pbuf = ld_volatile(&C->ps_cur);
     const unsigned lane = lane_id();
     for (unsigned t = T.wid(); t < nt; t += T.nwarps()) {
       const uint32_t v = A.touched[t];
@@ -526,7 +738,7 @@ struct Search {
           cur_c = A.cnext[cur_c];
           ++nb;
         }
-        merge_batch(v, mine, nb, cur, psnap);
+        merge_batch(v, mine, nb, cur, psnap, pmark, pcount, pntiles, pbuf);
       }
     }
   }
@@ -638,10 +850,17 @@ __device__ void run_query(const GraphDev& G, const QArena& A, QCtl* C, const QPa
     const unsigned n_in = *reinterpret_cast<const volatile unsigned*>(&C->open_count[cur]);
     if (n_in == 0) break;
     if (T.leader() && globaltimer() - C->t_start > P.time_limit_ns) set_error(C, OPMOS_ERR_TIMEOUT);
-    const unsigned base = *reinterpret_cast<const volatile unsigned*>(&C->min_key[cur]);
-    X.phase_hist(T, cur, n_in, base);
+    const unsigned long long base = ld_volatile64(&C->min_key[cur]);
+    BinParams bp;
+    bp.b0 = (uint32_t)(base >> 32);
+    bp.b1 = (uint32_t)base;
+    bp.delta = P.delta;
+    bp.s1 = 0;
+    for (unsigned sp = ld_volatile(&C->f1span[cur]); (sp >> bp.s1) >= (unsigned)kNB1; ++bp.s1) {
+    }
+    X.phase_hist(T, cur, n_in, bp);
     if (!(ok = T.sync(C))) break;
-    X.phase_extract(T, cur, n_in, base);
+    X.phase_extract(T, cur, n_in, bp);
     if (!(ok = T.sync(C))) break;
     X.phase_expand(T, nxt);
     if (!(ok = T.sync(C))) break;
