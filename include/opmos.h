@@ -70,7 +70,7 @@ typedef struct opmos_server opmos_server;
 typedef struct opmos_options {
   uint32_t window;           /* W: target number of labels extracted per step (the NUM_POP of
                                 Algorithm 2, Sec. 5). Steps take whole F[0] buckets, so a step
-                                may take fewer (never more than 4W). Default 4096 (single query),
+                                may take fewer (never more than 4W). Default 1024 (single query),
                                 256 (batch). */
   uint32_t lanes_per_label;  /* threads that expand one label's out-arcs: 4, 8, 16 or 32.
                                 Default 8. */
@@ -105,6 +105,8 @@ typedef struct opmos_stats {
   uint64_t heuristic_ns;   /* device time of the heuristic kernel(s) */
   uint64_t search_ns;      /* device time of the search kernel(s) */
   uint64_t total_ns;       /* host wall time of the call */
+  uint64_t phase_ns[4];    /* device time per search phase (histogram, extract+expand, merge,
+                              output), as seen by the leading thread, barrier waits included */
 } opmos_stats;
 
 /* Fill *opt with the defaults (all fields explicit). */

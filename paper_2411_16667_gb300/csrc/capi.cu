@@ -286,6 +286,10 @@ void fill_stats(opmos_stats* s, const QResult& R, uint32_t D) {
   s->steps = R.stats[S_STEPS];
   s->frontier_cmp = R.stats[S_FCMP];
   s->p_cmp = R.stats[S_PCMP];
+  s->phase_ns[0] = R.stats[S_THIST];
+  s->phase_ns[1] = R.stats[S_TEXPAND];
+  s->phase_ns[2] = R.stats[S_TMERGE];
+  s->phase_ns[3] = R.stats[S_TOUT];
   // algorithmic bytes: per extracted label 8d+12 (g, node, rowptr pair, F key),
   // per candidate 4+8d (col, cost, h), per compared frontier/P entry 4d, per
   // inserted label 4d+24 (label record, frontier slot, OPEN entry), per prune 4.
@@ -415,7 +419,7 @@ int solve_one(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint
 
   int occ = search_occupancy(D, 0);
   if (occ <= 0) return fail(OPMOS_ERR_CUDA, "search kernel cannot be resident");
-  const unsigned blocks = (unsigned)di.sms * (unsigned)std::min(occ, 2);
+  const unsigned blocks = (unsigned)di.sms;  // one block of kGridThreads per SM
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -452,7 +456,7 @@ extern "C" {
 void opmos_default_options(opmos_options* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
-  o->window = 4096;
+  o->window = 1024;
   o->lanes_per_label = 8;
   o->tile = 32;
   o->delta = 1;

@@ -41,8 +41,14 @@ enum StatIdx {
   S_STEPS,
   S_FCMP,
   S_PCMP,
+  S_THIST,    // device ns spent in phase 1 (leader's view, barrier included)
+  S_TEXPAND,  // phase 2
+  S_TMERGE,   // phase 4
+  S_TOUT,     // output
   kNStat
 };
+
+constexpr unsigned kGridThreads = 512;  // threads per block of the single-query grid
 
 struct GraphDev {
   uint32_t n, m, d, maxdeg;
@@ -65,6 +71,7 @@ struct QCtl {
   unsigned win_count;
   unsigned cand_count;
   unsigned touched_count;
+  unsigned merge_next;    // next touched node to merge (dynamic scheduling)
   unsigned theta;
   unsigned plog_len;
   unsigned plog_snap;

@@ -208,6 +208,11 @@ struct Search {
         C->open_count[0] = 0;
         C->min_key[0] = ~0ull;
       }
+      if (s == t) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) A.plog[(size_t)k * A.plog_cap] = 0;
+        C->plog_len = 1;
+      }
       C->open_count[1] = 0;
       C->min_key[1] = ~0ull;
       C->f1span[0] = C->f1span[1] = 0;
@@ -217,15 +222,18 @@ struct Search {
     }
   }
 
-  // ---------------- phase 1: bucket histogram of OPEN ----------------
+  // ---------------- phase 1: bucket histogram of the live OPEN entries ----------------
   template <class Team>
   __device__ void phase_hist(const Team& T, unsigned cur, unsigned n_in, const BinParams& bp) {
     for (unsigned i = threadIdx.x; i < kNB; i += blockDim.x) S.hist[i] = 0;
     if (threadIdx.x == 0) S.span = 0;
+    if (T.leader_block()) publish_p_index();
     __syncthreads();
     const uint64_t* in = A.okey[cur];
+    const uint32_t* in_id = A.oid[cur];
     unsigned span = 0;
     for (unsigned i = T.tid(); i < n_in; i += T.nthreads()) {
+      if (A.lstatus[in_id[i]] == ST_DEAD) continue;  // pruned while open: not counted
       const uint64_t key = in[i];
       const unsigned b = bin_of(key, bp);
       atomicAdd(&S.hist[b], 1u);
@@ -245,35 +253,46 @@ struct Search {
       C->win_count = 0;
       C->cand_count = 0;
       C->touched_count = 0;
+      C->merge_next = 0;
     }
     if (T.leader_block()) plan_p_index();
   }
 
-  // Decide whether this step rebuilds the P index (P grew by ~1/8 since the
-  // last build) and fix the per-objective shifts that balance the Z-order.
+  // A rebuild planned in step s is ranked in phase 2 and tiled in phase 4 of
+  // step s; it becomes the live index here, at the start of step s+1.
+  __device__ void publish_p_index() {
+    if (threadIdx.x == 0 && C->ps_build) {
+      C->ps_cur = C->ps_nb;
+      C->ps_count = C->ps_src;
+      C->ps_ntiles = (C->ps_src + 31) / 32;
+      C->ps_mark = C->ps_mark_new;
+      C->ps_nbuild++;
+      C->ps_build = 0;
+    }
+  }
+
+  // Decide whether this step rebuilds the P index (the P log grew by ~1/8
+  // since the last build) and fix the per-objective shifts that balance the
+  // Z-order. The index covers log[0, mark); the rest is scanned directly.
   __device__ void plan_p_index() {
+    __syncthreads();
     if (D < 2) return;
     const unsigned plen = ld_volatile(&C->plog_len);
-    const unsigned k = A.fcount[P.goal];
-    const bool build = plen - C->ps_mark > 32u + C->ps_count / 8u && k > 0 && k <= kPSMax;
-    if (threadIdx.x == 0) {
-      C->ps_build = build;
-      S.pmax[0] = S.pmax[1] = S.pmax[2] = 0;
-    }
-    if (!build) return;
+    const bool build = plen - C->ps_mark > 32u + C->ps_count / 8u && plen <= kPSMax;
+    if (threadIdx.x == 0) S.pmax[0] = S.pmax[1] = S.pmax[2] = 0;
     __syncthreads();
+    if (!build) return;
     constexpr int MD = D - 1 < 3 ? D - 1 : 3;
-    const uint64_t fb = A.fbase[P.goal];
-    const unsigned cap = A.fcap[P.goal];
     unsigned mx[3] = {0, 0, 0};
-    for (unsigned i = threadIdx.x; i < k; i += blockDim.x)
+    for (unsigned i = threadIdx.x; i < plen; i += blockDim.x)
 #pragma unroll
-      for (int j = 0; j < MD; ++j) mx[j] = max(mx[j], A.fpool[fb + (size_t)(j + 1) * cap + i] - hk(j + 1, P.start));
+      for (int j = 0; j < MD; ++j)
+        mx[j] = max(mx[j], A.plog[(size_t)(j + 1) * A.plog_cap + i] - hk(j + 1, P.start));
 #pragma unroll
     for (int j = 0; j < MD; ++j) atomicMax(&S.pmax[j], mx[j]);
     __syncthreads();
     if (threadIdx.x == 0) {
-      int bl[3], mn = 32;
+      int bl[3] = {0, 0, 0}, mn = 32;
 #pragma unroll
       for (int j = 0; j < MD; ++j) {
         bl[j] = 32 - __clz(S.pmax[j]);
@@ -281,22 +300,21 @@ struct Search {
       }
 #pragma unroll
       for (int j = 0; j < 3; ++j) C->ps_shift[j] = j < MD ? (unsigned)(bl[j] - mn) : 0u;
-      C->ps_src = k;
+      C->ps_src = plen;
       C->ps_mark_new = plen;
       C->ps_nb = C->ps_cur ^ 1u;
+      C->ps_build = 1;
     }
   }
 
-  // Phase 2 part of a rebuild: rank every P entry in Z-order and scatter it
-  // into the idle index buffer.
+  // Phase 2 part of a rebuild: rank every logged goal cost in Z-order and
+  // scatter it into the idle index buffer.
   template <class Team>
   __device__ void build_p_rank(const Team& T) {
     if constexpr (D >= 2) {
       constexpr int MD = D - 1 < 3 ? D - 1 : 3;
       if (!ld_volatile(&C->ps_build)) return;
       const unsigned k = C->ps_src;
-      const uint64_t fb = A.fbase[P.goal];
-      const unsigned cap = A.fcap[P.goal];
       const unsigned nb = C->ps_nb;
       uint32_t lo[MD], sh[MD];
 #pragma unroll
@@ -304,24 +322,25 @@ struct Search {
         lo[j] = hk(j + 1, P.start);
         sh[j] = C->ps_shift[j];
       }
+      const size_t pc = A.plog_cap;
       for (unsigned i = T.tid(); i < k; i += T.nthreads()) {
         uint32_t zi[MD];
 #pragma unroll
-        for (int j = 0; j < MD; ++j) zi[j] = (A.fpool[fb + (size_t)(j + 1) * cap + i] - lo[j]) >> sh[j];
+        for (int j = 0; j < MD; ++j) zi[j] = (A.plog[(size_t)(j + 1) * pc + i] - lo[j]) >> sh[j];
         unsigned rank = 0;
         for (unsigned q = 0; q < k; ++q) {
           uint32_t zq[MD];
 #pragma unroll
-          for (int j = 0; j < MD; ++j) zq[j] = (A.fpool[fb + (size_t)(j + 1) * cap + q] - lo[j]) >> sh[j];
+          for (int j = 0; j < MD; ++j) zq[j] = (A.plog[(size_t)(j + 1) * pc + q] - lo[j]) >> sh[j];
           rank += z_less<MD>(zq, zi) || (q < i && !z_less<MD>(zi, zq));
         }
 #pragma unroll
-        for (int kk = 0; kk < D; ++kk) A.ps[nb][(size_t)kk * A.plog_cap + rank] = A.fpool[fb + (size_t)kk * cap + i];
+        for (int kk = 0; kk < D; ++kk) A.ps[nb][(size_t)kk * pc + rank] = A.plog[(size_t)kk * pc + i];
       }
     }
   }
 
-  // Phase 3 part of a rebuild: tile minima, then publish the new index.
+  // Phase 4 part of a rebuild: tile minima of the idle buffer.
   template <class Team>
   __device__ void build_p_tiles(const Team& T) {
     if constexpr (D >= 2) {
@@ -339,13 +358,6 @@ struct Search {
           for (int kk = 0; kk < D; ++kk) mn[kk] = min(mn[kk], A.ps[nb][(size_t)kk * A.plog_cap + e]);
 #pragma unroll
         for (int kk = 0; kk < D; ++kk) A.pst[nb][(size_t)kk * tcap + t] = mn[kk];
-      }
-      if (T.leader()) {
-        C->ps_cur = nb;
-        C->ps_count = k;
-        C->ps_ntiles = nt;
-        C->ps_mark = C->ps_mark_new;
-        C->ps_nbuild++;
       }
     }
   }
@@ -390,53 +402,111 @@ struct Search {
     return bstar;
   }
 
-  // ---------------- phase 2: extraction (Algorithm 2 l.9-16) ----------------
+  // n-th (0-based) set bit of m, 32 if there is none.
+  __device__ __forceinline__ unsigned nth_bit(unsigned m, unsigned n) {
+    for (unsigned i = 0; i < n && m; ++i) m &= m - 1;
+    return m ? __ffs(m) - 1 : 32u;
+  }
+
+  // Expansion of one window label by the L lanes of a lane group (Algorithm 1
+  // l.15-17): g' = g + c(e) for every out-arc, dropped when h(v') is infinite.
+  __device__ void expand_label(uint32_t id, unsigned gl, unsigned L) {
+    const uint32_t v = A.lnode[id];
+    uint32_t g[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) g[k] = A.lg[(size_t)k * A.label_cap + id];
+    const uint32_t e0 = __ldg(G.rowptr + v), e1 = __ldg(G.rowptr + v + 1);
+    for (uint32_t e = e0 + gl; e < e1; e += L) {
+      const uint32_t v2 = __ldg(G.col + e);
+      st[S_CAND]++;
+      if (hk(0, v2) == kInf) continue;  // goal unreachable from v2
+      const unsigned c = agg_inc(&C->cand_count);
+      A.cnode[c] = v2;
+      A.cparent[c] = id;
+      A.cedge[c] = e;
+#pragma unroll
+      for (int k = 0; k < D; ++k) A.cg[(size_t)k * A.cand_cap + c] = g[k] + __ldg(G.cost + (size_t)k * G.m + e);
+      const int old = atomicExch(&A.node_head[v2], (int)c);
+      A.cnext[c] = old;
+      if (old == kNil) A.touched[agg_inc(&C->touched_count)] = v2;
+    }
+  }
+
+  // ---------------- phase 2: extraction + expansion (Algorithm 2 l.9-16) ----------------
+  // A warp reads 32 OPEN entries at a time: dead entries are dropped (lazy OPEN
+  // delete), entries in the window whose F a solution weakly dominates are
+  // dropped (lazy PruneOPEN), the other window entries are closed and expanded
+  // at once by lane groups; the rest is copied to the next OPEN.
   template <class Team>
-  __device__ void phase_extract(const Team& T, unsigned cur, unsigned n_in, const BinParams& bp) {
+  __device__ void phase_extract_expand(const Team& T, unsigned cur, unsigned n_in, const BinParams& bp) {
     const unsigned bstar = select_bucket(cur);
-    if (T.leader()) C->theta = bstar;
     const unsigned nxt = cur ^ 1u;
+    for (unsigned i = T.tid(); i < kNB; i += T.nthreads()) A.hist[nxt * kNB + i] = 0;
+    if (T.leader()) {
+      C->theta = bstar;
+      C->plog_snap = ld_volatile(&C->plog_len);
+      C->f1span[cur] = 0;  // measured again by the next step's phase 1
+    }
     const uint64_t* in = A.okey[cur];
     const uint32_t* in_id = A.oid[cur];
     uint64_t* out = A.okey[nxt];
     uint32_t* out_id = A.oid[nxt];
-    const unsigned plen = *reinterpret_cast<const volatile unsigned*>(&C->plog_len);
-    unsigned long long kmin = ~0ull;
-    for (unsigned i = T.tid(); i < n_in; i += T.nthreads()) {
-      const uint64_t key = in[i];
-      const unsigned id = in_id[i];
-      bool keep = true;
-      if (bin_of(key, bp) <= bstar) {
-        keep = false;
-        const uint8_t s = A.lstatus[id];
-        if (s == ST_DEAD) {
+    const unsigned plen = ld_volatile(&C->plog_len);
+    const unsigned pcount = ld_volatile(&C->ps_count);
+    const unsigned pmark = ld_volatile(&C->ps_mark);
+    const unsigned pntiles = ld_volatile(&C->ps_ntiles);
+    const unsigned pbuf = ld_volatile(&C->ps_cur);
+    const unsigned lane = lane_id();
+    const unsigned L = P.lanes, G_per = 32 / L, grp = lane / L, gl = lane % L;
+    unsigned long long kmin = ~0ull, pcmp = 0;
+    for (unsigned base = T.wid() * 32; base < n_in; base += T.nwarps() * 32) {
+      const unsigned i = base + lane;
+      const bool valid = i < n_in;
+      uint64_t key = 0;
+      uint32_t id = 0;
+      bool keep = false, want = false;
+      if (valid) {
+        key = in[i];
+        id = in_id[i];
+        if (A.lstatus[id] == ST_DEAD)
           st[S_DEAD]++;
+        else if (bin_of(key, bp) <= bstar)
+          want = true;
+        else
+          keep = true;
+      }
+      // lazy PruneOPEN: F against the goal costs logged since the label's
+      // last check (through the P index when that check predates it)
+      uint32_t F[D];
+      unsigned since = kInf;
+      if (want) {
+        const uint32_t v = A.lnode[id];
+#pragma unroll
+        for (int k = 0; k < D; ++k) F[k] = A.lg[(size_t)k * A.label_cap + id] + hk(k, v);
+        since = A.lpver[id];
+      } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) F[k] = 0;
+      }
+      since = warp_min(since);
+      bool alive = want;
+      if (since < plen) {
+        if (pcount && since < pmark)
+          p_filter(alive, F, pmark, plen, pcount, pntiles, pbuf, pcmp);
+        else
+          p_filter(alive, F, since, plen, 0, 0, 0, pcmp);
+      }
+      bool take = false;
+      if (want && !alive) {
+        A.lstatus[id] = ST_DEAD;
+        st[S_GOALPRUNED]++;
+      } else if (want) {
+        if (agg_inc(&C->win_count) < A.win_cap) {
+          A.lstatus[id] = ST_CLOSED;
+          st[S_EXTRACTED]++;
+          take = true;
         } else {
-          const uint32_t v = A.lnode[id];
-          uint32_t F[D];
-#pragma unroll
-          for (int k = 0; k < D; ++k) F[k] = A.lg[(size_t)k * A.label_cap + id] + hk(k, v);
-          bool dom = false;
-          for (unsigned j = A.lpver[id]; j < plen && !dom; ++j) {
-            uint32_t p[D];
-#pragma unroll
-            for (int k = 0; k < D; ++k) p[k] = A.plog[(size_t)k * A.plog_cap + j];
-            dom = weakly_le<D>(p, F);
-            st[S_PCMP]++;
-          }
-          if (dom) {
-            A.lstatus[id] = ST_DEAD;
-            st[S_GOALPRUNED]++;
-          } else {
-            const unsigned w = agg_inc(&C->win_count);
-            if (w < A.win_cap) {
-              A.window[w] = id;
-              A.lstatus[id] = ST_CLOSED;
-              st[S_EXTRACTED]++;
-            } else {
-              keep = true;  // window full: stays in OPEN for the next step
-            }
-          }
+          keep = true;  // window full: stays in OPEN for the next step
         }
       }
       if (keep) {
@@ -449,47 +519,86 @@ struct Search {
           set_error(C, OPMOS_ERR_CAPACITY);
         }
       }
+      unsigned hits = __ballot_sync(0xffffffffu, take);
+      while (hits) {
+        const unsigned src = nth_bit(hits, grp);
+        const uint32_t lid = __shfl_sync(0xffffffffu, id, src < 32 ? src : 0);
+        if (src < 32) expand_label(lid, gl, L);
+        for (unsigned r = 0; r < G_per && hits; ++r) hits &= hits - 1;
+      }
     }
+    if (lane == 0) st[S_PCMP] += pcmp;
     kmin = warp_min64(kmin);
-    if (lane_id() == 0 && kmin != ~0ull) atomicMin(&C->min_key[nxt], kmin);
+    if (lane == 0 && kmin != ~0ull) atomicMin(&C->min_key[nxt], kmin);
     build_p_rank(T);
   }
 
-  // ---------------- phase 3: expansion (Algorithm 1 l.15-17) ----------------
-  template <class Team>
-  __device__ void phase_expand(const Team& T, unsigned nxt) {
-    // the histogram of the next step starts from zero
-    for (unsigned i = T.tid(); i < kNB; i += T.nthreads()) A.hist[nxt * kNB + i] = 0;
-    if (T.leader()) {
-      C->plog_snap = *reinterpret_cast<const volatile unsigned*>(&C->plog_len);
-      C->f1span[nxt ^ 1u] = 0;  // measured again by the next step's phase 1
+  // F against the P index + the recent goal costs log[t0, t1): clears alive
+  // for candidates a solution weakly dominates (Algorithm 1 l.19/29).
+  __device__ void p_filter(bool& alive, const uint32_t (&F)[D], unsigned t0, unsigned t1, unsigned pcount,
+                           unsigned pntiles, unsigned pbuf, unsigned long long& pcmp) {
+    const unsigned lane = lane_id();
+    for (unsigned j0 = t0; j0 < t1; j0 += 32) {
+      unsigned amask = __ballot_sync(0xffffffffu, alive);
+      if (!amask) return;
+      const unsigned jj = j0 + lane;
+      const bool vp = jj < t1;
+      uint32_t p[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) p[k] = vp ? A.plog[(size_t)k * A.plog_cap + jj] : kInf;
+      pcmp += (unsigned long long)__popc(amask) * min(32u, t1 - j0);
+      while (amask) {
+        const unsigned j = __ffs(amask) - 1;
+        amask &= amask - 1;
+        uint32_t Fj[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) Fj[k] = __shfl_sync(0xffffffffu, F[k], j);
+        const bool wd = vp && weakly_le<D>(p, Fj);
+        if (__ballot_sync(0xffffffffu, wd) && lane == j) alive = false;
+      }
     }
-    build_p_tiles(T);
-    const unsigned nw = min(*reinterpret_cast<const volatile unsigned*>(&C->win_count), A.win_cap);
-    const unsigned L = P.lanes;
-    const unsigned gl = T.tid() % L;
-    const unsigned ngroups = T.nthreads() / L;
-    for (unsigned w = T.tid() / L; w < nw; w += ngroups) {
-      const uint32_t id = A.window[w];
-      const uint32_t v = A.lnode[id];
-      uint32_t g[D];
+    if (!pcount) return;
+    const uint32_t* ps = A.ps[pbuf];
+    const uint32_t* pst = A.pst[pbuf];
+    const size_t tcap = A.plog_cap / 32 + 1;
+    constexpr int U = 4;  // tile-minimum groups loaded per round
+    for (unsigned tg0 = 0; tg0 < pntiles; tg0 += 32 * U) {
+      if (!__any_sync(0xffffffffu, alive)) return;
+      uint32_t tm[U][D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) g[k] = A.lg[(size_t)k * A.label_cap + id];
-      const uint32_t e0 = __ldg(G.rowptr + v), e1 = __ldg(G.rowptr + v + 1);
-      for (uint32_t e = e0 + gl; e < e1; e += L) {
-        const uint32_t v2 = __ldg(G.col + e);
-        st[S_CAND]++;
-        if (hk(0, v2) == kInf) continue;  // goal unreachable from v2
-        const unsigned c = agg_inc(&C->cand_count);
-        A.cnode[c] = v2;
-        A.cparent[c] = id;
-        A.cedge[c] = e;
+      for (int u = 0; u < U; ++u) {
+        const unsigned tl = tg0 + u * 32 + lane;
 #pragma unroll
-        for (int k = 0; k < D; ++k)
-          A.cg[(size_t)k * A.cand_cap + c] = g[k] + __ldg(G.cost + (size_t)k * G.m + e);
-        const int old = atomicExch(&A.node_head[v2], (int)c);
-        A.cnext[c] = old;
-        if (old == kNil) A.touched[agg_inc(&C->touched_count)] = v2;
+        for (int k = 0; k < D; ++k) tm[u][k] = tl < pntiles ? pst[(size_t)k * tcap + tl] : kInf;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const unsigned tg = tg0 + u * 32;
+        unsigned amask = __ballot_sync(0xffffffffu, alive);
+        if (tg >= pntiles || !amask) break;
+        const bool vt = tg + lane < pntiles;
+        while (amask) {
+          const unsigned j = __ffs(amask) - 1;
+          amask &= amask - 1;
+          uint32_t Fj[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) Fj[k] = __shfl_sync(0xffffffffu, F[k], j);
+          unsigned pm = __ballot_sync(0xffffffffu, vt && weakly_le<D>(tm[u], Fj));
+          pcmp += min(32u, pntiles - tg);
+          bool dead = false;
+          while (pm && !dead) {
+            const unsigned tt = __ffs(pm) - 1;
+            pm &= pm - 1;
+            const unsigned e = (tg + tt) * 32 + lane;
+            const bool ve = e < pcount;
+            uint32_t p[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) p[k] = ve ? ps[(size_t)k * A.plog_cap + e] : kInf;
+            dead = __ballot_sync(0xffffffffu, ve && weakly_le<D>(p, Fj)) != 0;
+            pcmp += 32;
+          }
+          if (dead && lane == j) alive = false;
+        }
       }
     }
   }
@@ -505,125 +614,93 @@ struct Search {
 #pragma unroll
     for (int k = 0; k < D; ++k) c[k] = valid ? A.cg[(size_t)k * A.cand_cap + mine] : 0u;
     bool alive = valid;
-    // (a) in-batch: dominated or duplicate of an earlier candidate
+    // (a) in-batch: dominated by, or a duplicate of an earlier, candidate
     for (unsigned j = 0; j < nb; ++j) {
       uint32_t cj[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) cj[k] = __shfl_sync(0xffffffffu, c[k], j);
       if (alive && lane != j && (dominates<D>(cj, c) || (j < lane && equal<D>(cj, c)))) alive = false;
     }
-    // (b) against the frontier alpha(v), compacting it in place
     uint64_t fb = A.fbase[v];
     unsigned cap = A.fcap[v];
     const unsigned fc = A.fcount[v];
-    unsigned out = 0;
-    unsigned long long fcmp = 0, pruned_n = 0;
-    for (unsigned i0 = 0; i0 < fc; i0 += 32) {
-      const unsigned i = i0 + lane;
-      const bool vm = i < fc;
-      uint32_t m[D];
-      uint32_t mid = 0;
+    unsigned out = fc;
+    unsigned long long fcmp = 0, pruned_n = 0, pcmp = 0;
+    if (is_goal) {
+      // (b') at the goal alpha(v_g) is P: one weak-dominance test against the
+      // P index and every goal cost logged since it was built (this warp is
+      // the only writer of the log in this phase). P members a new solution
+      // dominates are dropped once, at output (Prune(P, l) of l.11).
+      const unsigned plen = ld_volatile(&C->plog_len);
+      p_filter(alive, c, pcount ? pmark : 0u, plen, pcount, pntiles, pbuf, pcmp);
+    } else {
+      // (b) against the frontier alpha(v), compacting it in place; four
+      // tiles of 32 entries are loaded per round
+      out = 0;
+      constexpr int U = 4;
+      bool done = false;
+      for (unsigned r0 = 0; r0 < fc && !done; r0 += 32 * U) {
+        uint32_t m[U][D];
+        uint32_t mid[U];
 #pragma unroll
-      for (int k = 0; k < D; ++k) m[k] = vm ? A.fpool[fb + (size_t)k * cap + i] : kInf;
-      if (vm) mid = A.fpool[fb + (size_t)D * cap + i];
-      bool pruned = false;
-      unsigned amask = __ballot_sync(0xffffffffu, alive);
-      if (amask == 0) {
-        // nothing left to test: the rest of the frontier is kept as is
-        if (out == i0) {
-          out = fc;
-          break;
+        for (int u = 0; u < U; ++u) {
+          const unsigned i = r0 + u * 32 + lane;
+          const bool vm = i < fc;
+#pragma unroll
+          for (int k = 0; k < D; ++k) m[u][k] = vm ? A.fpool[fb + (size_t)k * cap + i] : kInf;
+          mid[u] = vm ? A.fpool[fb + (size_t)D * cap + i] : 0u;
         }
-      }
-      fcmp += (unsigned long long)__popc(amask) * min(32u, fc - i0);
-      while (amask) {
-        const unsigned j = __ffs(amask) - 1;
-        amask &= amask - 1;
-        uint32_t cj[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) cj[k] = __shfl_sync(0xffffffffu, c[k], j);
-        const bool wd = vm && weakly_le<D>(m, cj);
-        if (__ballot_sync(0xffffffffu, wd) && lane == j) alive = false;
-        pruned |= vm && dominates<D>(cj, m);
-      }
-      const bool keep = vm && !pruned;
-      if (vm && pruned) {
-        A.lstatus[mid] = ST_DEAD;
-        pruned_n++;
-      }
-      const unsigned km = __ballot_sync(0xffffffffu, keep);
-      const unsigned pos = out + __popc(km & lanemask_lt());
-      __syncwarp();
-      if (keep && pos != i) {
-#pragma unroll
-        for (int k = 0; k < D; ++k) A.fpool[fb + (size_t)k * cap + pos] = m[k];
-        A.fpool[fb + (size_t)D * cap + pos] = mid;
-      }
-      __syncwarp();
-      out += __popc(km);
-    }
-    // (c) F against P (Algorithm 1 l.29); at the goal alpha(v_g) is P already.
-    // Recent goal costs are scanned directly, the rest through the P index.
-    unsigned long long pcmp = 0;
-    if (!is_goal && __any_sync(0xffffffffu, alive)) {
-      uint32_t F[D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) F[k] = c[k] + (valid ? hk(k, v) : 0u);
-      const unsigned t0 = pcount ? pmark : 0u;  // no index: scan the whole log
-      for (unsigned j0 = t0; j0 < psnap; j0 += 32) {
-        unsigned amask = __ballot_sync(0xffffffffu, alive);
-        if (!amask) break;
-        const unsigned jj = j0 + lane;
-        const bool vp = jj < psnap;
-        uint32_t p[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) p[k] = vp ? A.plog[(size_t)k * A.plog_cap + jj] : kInf;
-        pcmp += (unsigned long long)__popc(amask) * min(32u, psnap - j0);
-        while (amask) {
-          const unsigned j = __ffs(amask) - 1;
-          amask &= amask - 1;
-          uint32_t Fj[D];
-#pragma unroll
-          for (int k = 0; k < D; ++k) Fj[k] = __shfl_sync(0xffffffffu, F[k], j);
-          const bool wd = vp && weakly_le<D>(p, Fj);
-          if (__ballot_sync(0xffffffffu, wd) && lane == j) alive = false;
-        }
-      }
-      if (pcount) {
-        const uint32_t* ps = A.ps[pbuf];
-        const uint32_t* pst = A.pst[pbuf];
-        const size_t tcap = A.plog_cap / 32 + 1;
-        for (unsigned tg = 0; tg < pntiles; tg += 32) {
+        for (int u = 0; u < U; ++u) {
+          const unsigned i0 = r0 + u * 32;
+          if (i0 >= fc) {
+            done = true;
+            break;
+          }
+          const unsigned i = i0 + lane;
+          const bool vm = i < fc;
+          bool pruned = false;
           unsigned amask = __ballot_sync(0xffffffffu, alive);
-          if (!amask) break;
-          const unsigned tl = tg + lane;
-          const bool vt = tl < pntiles;
-          uint32_t tm[D];
-#pragma unroll
-          for (int k = 0; k < D; ++k) tm[k] = vt ? pst[(size_t)k * tcap + tl] : kInf;
+          if (amask == 0 && out == i0) {
+            // nothing left to test and nothing moved: the rest stays in place
+            out = fc;
+            done = true;
+            break;
+          }
+          fcmp += (unsigned long long)__popc(amask) * min(32u, fc - i0);
           while (amask) {
             const unsigned j = __ffs(amask) - 1;
             amask &= amask - 1;
-            uint32_t Fj[D];
+            uint32_t cj[D];
 #pragma unroll
-            for (int k = 0; k < D; ++k) Fj[k] = __shfl_sync(0xffffffffu, F[k], j);
-            unsigned pm = __ballot_sync(0xffffffffu, vt && weakly_le<D>(tm, Fj));
-            pcmp += min(32u, pntiles - tg);
-            bool dead = false;
-            while (pm && !dead) {
-              const unsigned tt = __ffs(pm) - 1;
-              pm &= pm - 1;
-              const unsigned e = (tg + tt) * 32 + lane;
-              const bool ve = e < pcount;
-              uint32_t p[D];
-#pragma unroll
-              for (int k = 0; k < D; ++k) p[k] = ve ? ps[(size_t)k * A.plog_cap + e] : kInf;
-              dead = __ballot_sync(0xffffffffu, ve && weakly_le<D>(p, Fj)) != 0;
-              pcmp += 32;
-            }
-            if (dead && lane == j) alive = false;
+            for (int k = 0; k < D; ++k) cj[k] = __shfl_sync(0xffffffffu, c[k], j);
+            const bool wd = vm && weakly_le<D>(m[u], cj);
+            if (__ballot_sync(0xffffffffu, wd) && lane == j) alive = false;
+            pruned |= vm && dominates<D>(cj, m[u]);
           }
+          const bool keep = vm && !pruned;
+          if (vm && pruned) {
+            A.lstatus[mid[u]] = ST_DEAD;
+            pruned_n++;
+          }
+          const unsigned km = __ballot_sync(0xffffffffu, keep);
+          const unsigned pos = out + __popc(km & lanemask_lt());
+          __syncwarp();
+          if (keep && pos != i) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) A.fpool[fb + (size_t)k * cap + pos] = m[u][k];
+            A.fpool[fb + (size_t)D * cap + pos] = mid[u];
+          }
+          __syncwarp();
+          out += __popc(km);
         }
+      }
+      // (c) F against P (Algorithm 1 l.29)
+      if (__any_sync(0xffffffffu, alive)) {
+        uint32_t F[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) F[k] = c[k] + (valid ? hk(k, v) : 0u);
+        p_filter(alive, F, pcount ? pmark : 0u, psnap, pcount, pntiles, pbuf, pcmp);
       }
     }
     // (d) survivors become labels, join alpha(v), OPEN (or the P log at the goal)
@@ -663,7 +740,7 @@ struct Search {
         }
         unsigned plen = 0;
         if (is_goal) {
-          plen = *reinterpret_cast<volatile unsigned*>(&C->plog_len);
+          plen = ld_volatile(&C->plog_len);
           if (plen + ns > A.plog_cap) {
             if (lane == 0) set_error(C, OPMOS_ERR_CAPACITY);
             return;
@@ -718,14 +795,18 @@ struct Search {
 
   template <class Team>
   __device__ void phase_merge(const Team& T, unsigned cur) {
-    const unsigned nt = *reinterpret_cast<const volatile unsigned*>(&C->touched_count);
-    const unsigned psnap = *reinterpret_cast<const volatile unsigned*>(&C->plog_snap);
+    const unsigned nt = ld_volatile(&C->touched_count);
+    const unsigned psnap = ld_volatile(&C->plog_snap);
     const unsigned pcount = ld_volatile(&C->ps_count);
     const unsigned pmark = ld_volatile(&C->ps_mark);
     const unsigned pntiles = ld_volatile(&C->ps_ntiles);
     const unsigned pbuf = ld_volatile(&C->ps_cur);
     const unsigned lane = lane_id();
-    for (unsigned t = T.wid(); t < nt; t += T.nwarps()) {
+    for (;;) {
+      unsigned t = 0;
+      if (lane == 0) t = atomicAdd(&C->merge_next, 1u);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (t >= nt) break;
       const uint32_t v = A.touched[t];
       int cur_c = A.node_head[v];
       __syncwarp();
@@ -741,29 +822,50 @@ struct Search {
         merge_batch(v, mine, nb, cur, psnap, pmark, pcount, pntiles, pbuf);
       }
     }
+    build_p_tiles(T);
   }
 
-  // ---------------- output: sorted P and its paths ----------------
+  // ---------------- output: P without dominated members, sorted, with paths ----------------
   template <class Team>
-  __device__ void output(const Team& T, QResult* R) {
+  __device__ bool output(const Team& T) {
     const uint32_t t = P.goal;
     const unsigned k = A.fcount[t];
     const uint64_t fb = A.fbase[t];
     const unsigned cap = A.fcap[t];
     const bool paths = !(P.flags & OPMOS_FLAG_NO_PATHS);
-    // region 1: costs (k*D, lexicographic) then path offsets (k+1)
-    if (T.leader()) {
-      const unsigned long long words = (unsigned long long)k * D + k + 1;
-      const unsigned long long off = atomicAdd(O.used, words);
-      if (off + words > O.cap) {
-        set_error(C, OPMOS_ERR_CAPACITY);
+    // (1) Prune(P, l) deferred from the search: drop members another member dominates
+    for (unsigned i = T.tid(); i < k; i += T.nthreads()) {
+      uint32_t ci[D];
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) ci[kk] = A.fpool[fb + (size_t)kk * cap + i];
+      bool dom = false;
+      for (unsigned j = 0; j < k && !dom; ++j) {
+        uint32_t cj[D];
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) cj[kk] = A.fpool[fb + (size_t)kk * cap + j];
+        dom = dominates<D>(cj, ci);
       }
-      C->res_off = off;
-      C->res_count = k;
+      if (dom) {
+        A.lstatus[A.fpool[fb + (size_t)D * cap + i]] = ST_DEAD;
+        st[S_PRUNED]++;
+      } else {
+        atomicAdd(&C->res_count, 1u);
+      }
     }
-    if (!T.sync(C)) return;
+    if (!T.sync(C)) return false;
+    // (2) region 1: costs (k'*D, lexicographic) then path offsets (k'+1)
+    const unsigned kk_live = ld_volatile(&C->res_count);
+    if (T.leader()) {
+      const unsigned long long words = (unsigned long long)kk_live * D + kk_live + 1;
+      const unsigned long long off = atomicAdd(O.used, words);
+      if (off + words > O.cap) set_error(C, OPMOS_ERR_CAPACITY);
+      C->res_off = off;
+    }
+    if (!T.sync(C)) return false;
     const unsigned long long off = C->res_off;
     for (unsigned i = T.tid(); i < k; i += T.nthreads()) {
+      const uint32_t idi = A.fpool[fb + (size_t)D * cap + i];
+      if (A.lstatus[idi] == ST_DEAD) continue;
       uint32_t ci[D];
 #pragma unroll
       for (int kk = 0; kk < D; ++kk) ci[kk] = A.fpool[fb + (size_t)kk * cap + i];
@@ -772,32 +874,34 @@ struct Search {
         uint32_t cj[D];
 #pragma unroll
         for (int kk = 0; kk < D; ++kk) cj[kk] = A.fpool[fb + (size_t)kk * cap + j];
-        rank += lex_less<D>(cj, ci);
+        if ((lex_less<D>(cj, ci) || (j < i && equal<D>(cj, ci))) &&
+            A.lstatus[A.fpool[fb + (size_t)D * cap + j]] != ST_DEAD)
+          ++rank;
       }
 #pragma unroll
       for (int kk = 0; kk < D; ++kk) O.words[off + (size_t)rank * D + kk] = ci[kk];
       unsigned len = 0;
-      if (paths) {
-        for (uint32_t x = A.fpool[fb + (size_t)D * cap + i]; x != kInf; x = A.lparent[x]) ++len;
-      }
-      O.words[off + (size_t)k * D + rank] = len;
+      if (paths)
+        for (uint32_t x = idi; x != kInf; x = A.lparent[x]) ++len;
+      O.words[off + (size_t)kk_live * D + rank] = len;
+      A.lpver[idi] = rank;  // remembered for the path pass
     }
-    if (!T.sync(C)) return;
-    // exclusive scan of path lengths by the leader block, then allocate region 2
+    if (!T.sync(C)) return false;
+    // (3) exclusive scan of path lengths by the leader block, then region 2
     if (T.leader_block()) {
-      uint32_t* lens = O.words + off + (size_t)k * D;
+      uint32_t* lens = O.words + off + (size_t)kk_live * D;
       unsigned carry = 0;
-      for (unsigned b0 = 0; b0 < k + 1; b0 += blockDim.x) {
+      for (unsigned b0 = 0; b0 < kk_live + 1; b0 += blockDim.x) {
         const unsigned i = b0 + threadIdx.x;
-        const unsigned x = i < k ? lens[i] : 0;
+        const unsigned x = i < kk_live ? lens[i] : 0;
         unsigned total;
         const unsigned ex = block_exclusive_scan(x, S.warp, total);
-        if (i <= k) lens[i] = carry + ex;
+        if (i <= kk_live) lens[i] = carry + ex;
         carry += total;
       }
       if (threadIdx.x == 0) {
         const unsigned long long total = carry;
-        const unsigned long long words = paths ? 2 * total - k : 0;
+        const unsigned long long words = paths ? 2 * total - kk_live : 0;
         unsigned long long p0 = 0;
         if (words) {
           p0 = atomicAdd(O.used, words);
@@ -807,31 +911,25 @@ struct Search {
         C->res_total = total;
       }
     }
-    if (!T.sync(C)) return;
+    if (!T.sync(C)) return false;
     if (paths) {
       const unsigned long long p0 = C->res_path, total = C->res_total;
-      const uint32_t* offs = O.words + off + (size_t)k * D;
+      const uint32_t* offs = O.words + off + (size_t)kk_live * D;
       for (unsigned i = T.tid(); i < k; i += T.nthreads()) {
-        uint32_t ci[D];
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) ci[kk] = A.fpool[fb + (size_t)kk * cap + i];
-        unsigned rank = 0;
-        for (unsigned j = 0; j < k; ++j) {
-          uint32_t cj[D];
-#pragma unroll
-          for (int kk = 0; kk < D; ++kk) cj[kk] = A.fpool[fb + (size_t)kk * cap + j];
-          rank += lex_less<D>(cj, ci);
-        }
+        const uint32_t idi = A.fpool[fb + (size_t)D * cap + i];
+        if (A.lstatus[idi] == ST_DEAD) continue;
+        const unsigned rank = A.lpver[idi];
         const unsigned a = offs[rank], b = offs[rank + 1];
         // nodes at p0 + [a, b); arcs at p0 + total + [a - rank, b - rank - 1)
         unsigned pos = b;
-        for (uint32_t x = A.fpool[fb + (size_t)D * cap + i]; x != kInf; x = A.lparent[x]) {
+        for (uint32_t x = idi; x != kInf && pos > a; x = A.lparent[x]) {
           --pos;
           O.words[p0 + pos] = A.lnode[x];
           if (A.lparent[x] != kInf) O.words[p0 + total + pos - rank - 1] = A.ledge[x];
         }
       }
     }
+    return true;
   }
 };
 
@@ -845,9 +943,17 @@ __device__ void run_query(const GraphDev& G, const QArena& A, QCtl* C, const QPa
   X.init(T, reset_ctl);
   bool ok = T.sync(C);
   unsigned step = 0;
+  unsigned long long tph = globaltimer();
+  auto lap = [&](int idx) {
+    if (T.leader()) {
+      const unsigned long long t = globaltimer();
+      X.st[idx] += t - tph;
+      tph = t;
+    }
+  };
   while (ok) {
-    const unsigned cur = step & 1u, nxt = cur ^ 1u;
-    const unsigned n_in = *reinterpret_cast<const volatile unsigned*>(&C->open_count[cur]);
+    const unsigned cur = step & 1u;
+    const unsigned n_in = ld_volatile(&C->open_count[cur]);
     if (n_in == 0) break;
     if (T.leader() && globaltimer() - C->t_start > P.time_limit_ns) set_error(C, OPMOS_ERR_TIMEOUT);
     const unsigned long long base = ld_volatile64(&C->min_key[cur]);
@@ -860,15 +966,20 @@ __device__ void run_query(const GraphDev& G, const QArena& A, QCtl* C, const QPa
     }
     X.phase_hist(T, cur, n_in, bp);
     if (!(ok = T.sync(C))) break;
-    X.phase_extract(T, cur, n_in, bp);
+    lap(S_THIST);
+    X.phase_extract_expand(T, cur, n_in, bp);
     if (!(ok = T.sync(C))) break;
-    X.phase_expand(T, nxt);
-    if (!(ok = T.sync(C))) break;
+    lap(S_TEXPAND);
     X.phase_merge(T, cur);
     if (!(ok = T.sync(C))) break;
+    lap(S_TMERGE);
     ++step;
   }
-  if (ok) X.output(T, R);
+  if (ok) {
+    if (T.leader()) C->res_count = 0;
+    ok = T.sync(C) && X.output(T);
+    lap(S_TOUT);
+  }
   X.st[S_STEPS] = T.leader() ? step : 0;
   flush_stats<Team>(C, X.st);
   T.sync(C);
@@ -886,7 +997,7 @@ __device__ void run_query(const GraphDev& G, const QArena& A, QCtl* C, const QPa
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) search_grid_kernel(GraphDev G, QArena A, QCtl* C, QParams P,
+__global__ void __launch_bounds__(kGridThreads, 1) search_grid_kernel(GraphDev G, QArena A, QCtl* C, QParams P,
                                                           OutPool O, QResult* R) {
   run_query<D>(G, A, C, P, O, GridTeam{}, R, false);
 }
@@ -921,7 +1032,7 @@ template <int D>
 static cudaError_t launch_grid_d(const GraphDev& G, const QArena& A, QCtl* C, const QParams& P,
                                  const OutPool& O, QResult* R, unsigned blocks, cudaStream_t s) {
   void* args[] = {(void*)&G, (void*)&A, (void*)&C, (void*)&P, (void*)&O, (void*)&R};
-  return cudaLaunchCooperativeKernel((void*)search_grid_kernel<D>, dim3(blocks), dim3(256), args, 0, s);
+  return cudaLaunchCooperativeKernel((void*)search_grid_kernel<D>, dim3(blocks), dim3(kGridThreads), args, 0, s);
 }
 
 template <int D>
@@ -936,7 +1047,7 @@ template <int D>
 static int occupancy_d(int which) {
   int nb = 0;
   if (which == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_grid_kernel<D>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_grid_kernel<D>, kGridThreads, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_batch_kernel<D>, 256, 0);
   return nb;

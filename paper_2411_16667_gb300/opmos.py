@@ -42,10 +42,13 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in (
         "extracted", "dead_skipped", "goal_pruned", "candidates", "inserted", "pruned", "steps",
-        "frontier_cmp", "p_cmp", "bytes", "heuristic_ns", "search_ns", "total_ns")]
+        "frontier_cmp", "p_cmp", "bytes", "heuristic_ns", "search_ns", "total_ns")] + [
+        ("phase_ns", ctypes.c_uint64 * 4)]
 
     def as_dict(self) -> dict:
-        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+        d = {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "phase_ns"}
+        d["phase_ns"] = [int(x) for x in self.phase_ns]
+        return d
 
 
 def lib(path: str | None = None):

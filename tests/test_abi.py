@@ -30,10 +30,10 @@ def test_library_builds_and_exports_every_symbol():
 
 def test_options_struct_matches_defaults():
     o = opmos.opmos_default_options()
-    assert (o.window, o.lanes_per_label, o.tile, o.delta) == (4096, 8, 32, 1)
+    assert (o.window, o.lanes_per_label, o.tile, o.delta) == (1024, 8, 32, 1)
     assert o.mem_budget_bytes == 8 << 30
     assert ctypes.sizeof(opmos.Options) == 48
-    assert ctypes.sizeof(opmos.Stats) == 13 * 8
+    assert ctypes.sizeof(opmos.Stats) == 17 * 8
 
 
 @pytest.mark.skipif(opmos.opmos_device_count() > 0, reason="only meaningful without a GPU")
