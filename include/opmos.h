@@ -134,6 +134,24 @@ OPMOS_API int opmos_heuristic(const opmos_graph* g, uint32_t goal, uint32_t d_us
 OPMOS_API int opmos_heuristic_copy(const opmos_heur* h, uint32_t* h_out);
 OPMOS_API void opmos_heuristic_destroy(opmos_heur* h);
 
+/* The heuristic of opmos_heuristic, written into a device buffer the caller
+ * owns, with no device memory allocated during the call. The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc while they
+ * run (all device memory reserved up front by their own pool allocator, or no
+ * tolerance for the allocation and implicit synchronisation it can cause).
+ *   h_out_device: device pointer to d_used*n uint32, layout as above
+ *     (d_used = 0 means all objectives); stream: cudaStream_t or NULL.
+ *   Limit: n <= 262144 nodes, else OPMOS_ERR_CAPACITY (use opmos_heuristic).
+ *   Scratch: one fixed array inside the library (about 10.5 MB, held by each
+ *     device that loads the library until exit). The first call on a device
+ *     looks up its address (cudaGetSymbolAddress) with that device current;
+ *     make that first call before any stream capture. Every call reuses the
+ *     same array, so calls that overlap on the GPU (other threads, other
+ *     streams) race: serialise them. The call returns when the result is
+ *     complete. Errors: INVALID_ARG, CAPACITY, TIMEOUT, CUDA. */
+OPMOS_API int opmos_heuristic_noalloc(const opmos_graph* g, uint32_t goal, uint32_t d_used,
+                                      uint32_t* h_out_device, void* stream);
+
 /* One start->goal query (Algorithm 2 semantics, exact result of Sec. 3).
  * heur may be NULL (computed here, its time reported in heuristic_ns); if
  * given it must belong to g and goal. opt may be NULL (defaults).

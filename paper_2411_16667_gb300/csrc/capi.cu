@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "opmos.h"
+#include "graph.cuh"
 #include "search.cuh"
 
 using namespace opmos;
@@ -99,14 +100,10 @@ T* carve(char*& p, size_t count, size_t align = 256) {
 
 }  // namespace
 
-struct opmos_graph {
-  uint32_t n = 0, d = 0, maxdeg = 0;
-  uint64_t m = 0;
-  uint32_t *rowptr = nullptr, *col = nullptr, *cost = nullptr;
-  uint32_t *rrowptr = nullptr, *rsrc = nullptr, *rcost = nullptr;
-  uint32_t* delta = nullptr;  // per objective, device
-  GraphDev dev{};
-};
+int opmos::record_error(int code, const char* msg) {
+  g_err = msg;
+  return code;
+}
 
 struct opmos_heur {
   const opmos_graph* g = nullptr;

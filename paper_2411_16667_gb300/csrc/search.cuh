@@ -37,6 +37,9 @@ struct HJob {
   uint32_t goal, k;
   uint32_t* h_out;  // n entries
 };
+// Sets the calling thread's opmos_last_error() message; returns code.
+int record_error(int code, const char* msg);
+
 cudaError_t launch_heuristic(const GraphDev& G, const HJob* jobs, unsigned njobs, uint32_t* scratch,
                              size_t scratch_words_per_block, unsigned blocks, const uint32_t* delta,
                              unsigned* next_job, unsigned* err, cudaStream_t s);

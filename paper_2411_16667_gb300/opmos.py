@@ -23,7 +23,8 @@ EXPORTS = ("opmos_default_options", "opmos_device_count", "opmos_graph_create", 
            "opmos_heuristic", "opmos_heuristic_copy", "opmos_heuristic_destroy", "opmos_solve",
            "opmos_solve_batch", "opmos_result_count", "opmos_result_d", "opmos_result_costs",
            "opmos_result_path", "opmos_result_stats", "opmos_result_free", "opmos_server_create",
-           "opmos_server_submit", "opmos_server_poll", "opmos_server_destroy", "opmos_last_error")
+           "opmos_server_submit", "opmos_server_poll", "opmos_server_destroy", "opmos_last_error",
+           "opmos_heuristic_noalloc")
 
 
 class OpmosError(RuntimeError):
@@ -88,6 +89,7 @@ def lib(path: str | None = None):
         L.opmos_server_destroy.argtypes = [vp]
         L.opmos_server_destroy.restype = None
         L.opmos_last_error.restype = ctypes.c_char_p
+        L.opmos_heuristic_noalloc.argtypes = [vp, u32, u32, vp, vp]
         _lib = L
     return _lib
 
@@ -168,6 +170,14 @@ class opmos_heur:
             self.close()
         except Exception:
             pass
+
+
+def opmos_heuristic_noalloc(graph: opmos_graph, goal: int, d_used: int, h_out_device_ptr: int,
+                            stream_ptr: int | None = None) -> None:
+    """Heuristic into a caller-owned device buffer; allocates nothing on the device."""
+    _check(lib().opmos_heuristic_noalloc(graph.handle, goal, d_used, ctypes.c_void_p(h_out_device_ptr),
+                                         ctypes.c_void_p(stream_ptr) if stream_ptr else None),
+           "opmos_heuristic_noalloc")
 
 
 @dataclasses.dataclass
