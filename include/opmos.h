@@ -80,7 +80,7 @@ typedef struct opmos_options {
   uint64_t label_budget;     /* max labels a query may create; exceeding it is
                                 OPMOS_ERR_BUDGET. Default: unlimited (arena-bound). */
   uint64_t mem_budget_bytes; /* device arena per query (single) or per batch (batch).
-                                Default: 8 GiB single, 24 GiB batch. */
+                                Default: 8 GiB single, 96 GiB batch. */
   uint32_t d_used;           /* use only the first d_used objectives (Table 1 order rule,
                                 Sec. 6.1). Default: all. */
   uint32_t flags;            /* OPMOS_FLAG_* */
@@ -107,6 +107,8 @@ typedef struct opmos_stats {
   uint64_t total_ns;       /* host wall time of the call */
   uint64_t phase_ns[4];    /* device time per search phase (histogram, extract+expand, merge,
                               output), as seen by the leading thread, barrier waits included */
+  uint64_t goal_inserted;  /* goal labels accepted into P during the search (before the final
+                              removal of dominated members) */
 } opmos_stats;
 
 /* Fill *opt with the defaults (all fields explicit). */
@@ -160,10 +162,14 @@ OPMOS_API int opmos_heuristic_noalloc(const opmos_graph* g, uint32_t goal, uint3
 OPMOS_API int opmos_solve(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint32_t goal,
                 const opmos_options* opt, opmos_result** out);
 
-/* nq independent queries in one persistent launch (one thread block per query,
- * queries pulled from a device-side counter). out receives nq results (each
- * may be NULL) and status[q] each query's own return code; the call returns
- * OPMOS_OK when the batch ran, even if some queries failed. */
+/* nq independent queries in one persistent cooperative launch with continuous
+ * batching: up to 192 queries run at once in their own arenas (each
+ * mem_budget_bytes / 192), all advancing one search step per grid iteration,
+ * and a finished query's slot is refilled from the queue at once. A query
+ * that outgrows its slot's arena is re-run alone with the single-query
+ * arena. out receives nq results (each may be NULL) and status[q] each
+ * query's own return code; the call returns OPMOS_OK when the batch ran, even
+ * if some queries failed. */
 OPMOS_API int opmos_solve_batch(const opmos_graph* g, uint32_t nq, const uint32_t* starts,
                       const uint32_t* goals, const opmos_options* opt, opmos_result** out,
                       int* status);

@@ -134,7 +134,7 @@ opmos_options resolve(const opmos_options* in, bool batch) {
   opmos_default_options(&o);
   if (batch) {
     o.window = 256;
-    o.mem_budget_bytes = 24ull << 30;
+    o.mem_budget_bytes = 96ull << 30;
   }
   if (!in) return o;
   if (in->window) o.window = in->window;
@@ -287,6 +287,7 @@ void fill_stats(opmos_stats* s, const QResult& R, uint32_t D) {
   s->phase_ns[1] = R.stats[S_TEXPAND];
   s->phase_ns[2] = R.stats[S_TMERGE];
   s->phase_ns[3] = R.stats[S_TOUT];
+  s->goal_inserted = R.stats[S_GOALINS];
   // algorithmic bytes: per extracted label 8d+12 (g, node, rowptr pair, F key),
   // per candidate 4+8d (col, cost, h), per compared frontier/P entry 4d, per
   // inserted label 4d+24 (label record, frontier slot, OPEN entry), per prune 4.
@@ -355,6 +356,7 @@ int search_status(unsigned st) {
 }
 
 constexpr unsigned long long kTimeLimitNs = 300ull * 1000 * 1000 * 1000;
+constexpr unsigned kBatchSlots = 192;  // concurrent queries of a batch
 constexpr size_t kOutWords = 64ull << 20;
 
 int solve_one(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint32_t goal, const opmos_options& o,
@@ -443,6 +445,149 @@ int solve_one(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint
   r->stats.total_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
                           std::chrono::steady_clock::now() - t0).count();
   *out = r;
+  return OPMOS_OK;
+}
+
+// h_0(start) of every query (its distance under objective 0), for ordering.
+__global__ void gather_h0_kernel(const MQuery* qs, unsigned nq, unsigned n, uint32_t* out) {
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nq) out[i] = qs[i].h[qs[i].start];
+}
+
+// One launch of the multi-query kernel over the queries in qlist, `slots` at a
+// time with `slot_budget` bytes each. Results go to out/status; queries that
+// outgrew their slot are listed in *overflow.
+int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const std::vector<uint32_t>& qlist,
+              const uint32_t* starts, const uint32_t* goals, uint32_t* hall, std::map<uint32_t, uint32_t>& gidx,
+              unsigned slots, size_t slot_budget, uint64_t hns, std::chrono::steady_clock::time_point t0,
+              opmos_result** out, int* status, std::vector<uint32_t>* overflow) {
+  const DevInfo di = device_info();
+  cudaStream_t s = (cudaStream_t)o.stream;
+  const uint32_t nq = (uint32_t)qlist.size();
+  const int occ = multi_occupancy();
+  if (occ <= 0) return fail(OPMOS_ERR_CUDA, "multi-query kernel cannot be resident");
+  const unsigned blocks = (unsigned)di.sms * (unsigned)std::min(occ, 2);
+  ArenaPlan pl;
+  if (int rc = plan_arena(g, D, o.window, slot_budget, true, &pl)) return rc;
+  const size_t slot_bytes = (pl.bytes + 255) / 256 * 256;
+  void* arena = nullptr;
+  if (int rc = g_arena.get(slot_bytes * slots, &arena)) return rc;
+  QParams P{};
+  P.window = o.window;
+  P.lanes = o.lanes_per_label;
+  P.delta = o.delta;
+  P.tile = o.tile;
+  P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, pl.label_cap);
+  P.flags = o.flags;
+  P.time_limit_ns = kTimeLimitNs;
+  std::vector<MSlot> hslots(slots);
+  for (unsigned i = 0; i < slots; ++i) {
+    MSlot& sl = hslots[i];
+    std::memset(&sl, 0, sizeof(sl));
+    layout_arena(g, D, pl, (char*)arena + i * slot_bytes, &sl.A);
+    sl.P = P;
+    sl.G = g->dev;
+    sl.d = D;
+    sl.state = SL_FREE;
+  }
+  std::vector<MQuery> qs(nq);
+  for (uint32_t i = 0; i < nq; ++i) {
+    const uint32_t q = qlist[i];
+    qs[i] = MQuery{0, starts[q], goals[q], D, hall + (size_t)gidx[goals[q]] * D * g->n};
+  }
+  // Longest first: admit queries in decreasing h_0(start) so that the large
+  // searches start early and overlap with many small ones.
+  std::vector<uint32_t> order(nq);
+  {
+    void* tmp = nullptr;
+    if (int rc = g_misc.get(nq * (sizeof(MQuery) + 4) + 512, &tmp)) return rc;
+    char* tp = (char*)tmp;
+    MQuery* tq = carve<MQuery>(tp, nq);
+    uint32_t* th = carve<uint32_t>(tp, nq);
+    std::vector<uint32_t> h0(nq);
+    CK(cudaMemcpyAsync(tq, qs.data(), nq * sizeof(MQuery), cudaMemcpyHostToDevice, s));
+    gather_h0_kernel<<<(nq + 255) / 256, 256, 0, s>>>(tq, nq, g->n, th);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h0.data(), th, nq * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (uint32_t i = 0; i < nq; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return h0[a] > h0[b]; });
+    std::vector<MQuery> sorted(nq);
+    for (uint32_t i = 0; i < nq; ++i) sorted[i] = qs[order[i]];
+    qs.swap(sorted);
+  }
+  // result pool: costs, offsets and paths of every query of this launch; a
+  // query that finds it full is reported as a capacity overflow and re-run
+  const size_t out_words = std::max<size_t>(kOutWords, std::min<size_t>((size_t)nq << 18, 1ull << 30));
+  void* outp = nullptr;
+  const size_t misc_bytes = slots * (sizeof(MSlot) + sizeof(QCtl)) + nq * (sizeof(MQuery) + sizeof(QResult)) +
+                            sizeof(GraphDev) + sizeof(MCtl) + 16 * 256;
+  if (int rc = g_out.get(out_words * 4 + misc_bytes, &outp)) return rc;
+  char* op = (char*)outp;
+  unsigned long long* used = carve<unsigned long long>(op, 1);
+  unsigned* qcount = carve<unsigned>(op, 1);
+  MCtl* M = carve<MCtl>(op, 1);
+  GraphDev* dgraphs = carve<GraphDev>(op, 1);
+  QCtl* ctls = carve<QCtl>(op, slots);
+  MSlot* dslots = carve<MSlot>(op, slots);
+  MQuery* dqs = carve<MQuery>(op, nq);
+  QResult* dres = carve<QResult>(op, nq);
+  uint32_t* words = carve<uint32_t>(op, out_words);
+  MCtl hM{};
+  hM.closing = 1;  // every query is queued up front
+  CK(cudaMemsetAsync(used, 0, 8, s));
+  CK(cudaMemcpyAsync(qcount, &nq, 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(M, &hM, sizeof(MCtl), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dgraphs, &g->dev, sizeof(GraphDev), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ctls, 0, slots * sizeof(QCtl), s));
+  CK(cudaMemsetAsync(dres, 0, nq * sizeof(QResult), s));
+  CK(cudaMemcpyAsync(dslots, hslots.data(), slots * sizeof(MSlot), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dqs, qs.data(), nq * sizeof(MQuery), cudaMemcpyHostToDevice, s));
+  OutPool O{words, out_words, used};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  cudaError_t e = launch_multi(dslots, ctls, slots, dqs, qcount, dgraphs, O, dres, M, blocks, s);
+  cudaEventRecord(e1, s);
+  std::vector<QResult> hres(nq);
+  MCtl hM2{};
+  cudaError_t e2 =
+      e == cudaSuccess ? cudaMemcpyAsync(hres.data(), dres, nq * sizeof(QResult), cudaMemcpyDeviceToHost, s) : e;
+  if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(&hM2, M, sizeof(MCtl), cudaMemcpyDeviceToHost, s);
+  cudaError_t e3 = cudaStreamSynchronize(s);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "multi-query launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "batch status copy");
+  if (e3 != cudaSuccess) return cuda_fail(e3, "multi-query kernel");
+  if (hM2.error) return fail((int)hM2.error, "multi-query kernel stopped with error %u", hM2.error);
+  const bool paths = !(o.flags & OPMOS_FLAG_NO_PATHS);
+  const uint64_t total_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                std::chrono::steady_clock::now() - t0).count();
+  for (uint32_t i = 0; i < nq; ++i) {
+    const uint32_t q = qlist[order[i]];
+    const unsigned st = hres[i].status;
+    if (st == OPMOS_ERR_CAPACITY) {
+      overflow->push_back(q);  // outgrew its slot: next round
+      continue;
+    }
+    if (st != 0) {
+      status[q] = (int)st;
+      continue;
+    }
+    opmos_result* r = nullptr;
+    int rc = take_result(hres[i], D, paths, words, s, &r);
+    status[q] = rc;
+    if (rc) continue;
+    fill_stats(&r->stats, hres[i], D);
+    r->stats.heuristic_ns = hns;
+    r->stats.search_ns = (uint64_t)(ms * 1e6);
+    r->stats.total_ns = total_ns;
+    out[q] = r;
+  }
   return OPMOS_OK;
 }
 
@@ -645,99 +790,29 @@ int opmos_solve_batch(const opmos_graph* g, uint32_t nq, const uint32_t* starts,
   } free_h{hall};
   uint64_t hns = 0;
   if (int rc = compute_heuristic(g, D, ugoals.data(), (uint32_t)ugoals.size(), hall, s, &hns)) return rc;
-  // slots: one thread block each, one arena each
-  int occ = search_occupancy(D, 1);
-  if (occ <= 0) return fail(OPMOS_ERR_CUDA, "batch kernel cannot be resident");
-  const unsigned slots = std::min<unsigned>(nq, (unsigned)di.sms * (unsigned)std::min(occ, 2));
-  ArenaPlan pl;
-  if (int rc = plan_arena(g, D, o.window, o.mem_budget_bytes / slots, true, &pl)) return rc;
-  const size_t slot_bytes = (pl.bytes + 255) / 256 * 256;
-  void* arena = nullptr;
-  if (int rc = g_arena.get(slot_bytes * slots, &arena)) return rc;
-  std::vector<QArena> arenas(slots);
-  for (unsigned i = 0; i < slots; ++i) layout_arena(g, D, pl, (char*)arena + i * slot_bytes, &arenas[i]);
-  std::vector<BatchQuery> qs(nq);
-  for (uint32_t q = 0; q < nq; ++q)
-    qs[q] = BatchQuery{starts[q], goals[q], hall + (size_t)gidx[goals[q]] * D * g->n};
-  const size_t out_words = std::max<size_t>(kOutWords, (size_t)nq * 4096);
-  void* outp = nullptr;
-  const size_t misc_bytes = slots * (sizeof(QArena) + sizeof(QCtl)) + nq * (sizeof(BatchQuery) + sizeof(QResult)) +
-                            8 * 256;
-  if (int rc = g_out.get(out_words * 4 + misc_bytes, &outp)) return rc;
-  char* op = (char*)outp;
-  unsigned long long* used = carve<unsigned long long>(op, 1);
-  unsigned* next_q = carve<unsigned>(op, 1);
-  QCtl* ctls = carve<QCtl>(op, slots);
-  QArena* darenas = carve<QArena>(op, slots);
-  BatchQuery* dqs = carve<BatchQuery>(op, nq);
-  QResult* dres = carve<QResult>(op, nq);
-  uint32_t* words = carve<uint32_t>(op, out_words);
-  CK(cudaMemsetAsync(used, 0, 8, s));
-  CK(cudaMemsetAsync(next_q, 0, 4, s));
-  CK(cudaMemsetAsync(ctls, 0, slots * sizeof(QCtl), s));
-  CK(cudaMemcpyAsync(darenas, arenas.data(), slots * sizeof(QArena), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(dqs, qs.data(), nq * sizeof(BatchQuery), cudaMemcpyHostToDevice, s));
-  QParams P{};
-  P.window = o.window;
-  P.lanes = o.lanes_per_label;
-  P.delta = o.delta;
-  P.tile = o.tile;
-  P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, pl.label_cap);
-  P.flags = o.flags;
-  P.time_limit_ns = kTimeLimitNs;
-  OutPool O{words, out_words, used};
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, s);
-  cudaError_t e = launch_search_batch(D, g->dev, darenas, ctls, dqs, nq, next_q, P, O, dres, slots, s);
-  cudaEventRecord(e1, s);
-  std::vector<QResult> hres(nq);
-  cudaError_t e2 =
-      e == cudaSuccess ? cudaMemcpyAsync(hres.data(), dres, nq * sizeof(QResult), cudaMemcpyDeviceToHost, s) : e;
-  cudaError_t e3 = cudaStreamSynchronize(s);
-  float ms = 0;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
-  if (e2 != cudaSuccess) return cuda_fail(e2, "batch status copy");
-  if (e3 != cudaSuccess) return cuda_fail(e3, "batch kernel");
-  const bool paths = !(o.flags & OPMOS_FLAG_NO_PATHS);
-  const uint64_t total_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
-                                std::chrono::steady_clock::now() - t0).count();
-  std::vector<uint32_t> retry;
-  for (uint32_t q = 0; q < nq; ++q) {
-    const unsigned st = hres[q].status;
-    if (st == OPMOS_ERR_CAPACITY) {
-      retry.push_back(q);  // outgrew its slot: re-run alone below
-      continue;
-    }
-    if (st != 0) {
-      status[q] = (int)st;
-      continue;
-    }
-    opmos_result* r = nullptr;
-    int rc = take_result(hres[q], D, paths, words, s, &r);
-    status[q] = rc;
-    if (rc) continue;
-    fill_stats(&r->stats, hres[q], D);
-    r->stats.heuristic_ns = hns;
-    r->stats.search_ns = (uint64_t)(ms * 1e6);
-    r->stats.total_ns = total_ns;
-    out[q] = r;
+  // Rounds of the multi-query kernel: all queries, then those that outgrew
+  // their slot with 8x fewer, 8x larger slots; single-query mode last.
+  std::vector<uint32_t> todo(nq);
+  for (uint32_t q = 0; q < nq; ++q) todo[q] = q;
+  unsigned slots = std::min<unsigned>(nq, std::min<unsigned>(kMaxSlots, kBatchSlots));
+  for (int round = 0; round < 3 && !todo.empty(); ++round) {
+    slots = std::max(1u, std::min<unsigned>(slots, (unsigned)todo.size()));
+    std::vector<uint32_t> overflow;
+    if (int rc = run_multi(g, D, o, todo, starts, goals, hall, gidx, slots, o.mem_budget_bytes / slots, hns, t0, out,
+                           status, &overflow))
+      return rc;
+    todo.swap(overflow);
+    slots = slots / 8;
+    if (slots < 2) break;
   }
-  // Queries whose front outgrew a batch slot run alone with a single-query
-  // arena (same options otherwise); their own status is reported.
-  if (!retry.empty()) {
+  if (!todo.empty()) {
     opmos_options so = resolve(opt, false);
     so.flags = o.flags;
     so.stream = o.stream;
-    if (opt && opt->mem_budget_bytes) so.mem_budget_bytes = std::max<uint64_t>(opt->mem_budget_bytes / 2, 1ull << 30);
-    for (uint32_t q : retry) {
+    if (opt && opt->mem_budget_bytes) so.mem_budget_bytes = std::max<uint64_t>(opt->mem_budget_bytes, 1ull << 30);
+    for (uint32_t q : todo) {
       opmos_result* r = nullptr;
-      const size_t hoff = (size_t)gidx[goals[q]] * D * g->n;
-      opmos_heur hh{g, goals[q], D, hall + hoff, 0};
+      opmos_heur hh{g, goals[q], D, hall + (size_t)gidx[goals[q]] * D * g->n, 0};
       const int rc = solve_one(g, &hh, starts[q], goals[q], so, D, &r);
       status[q] = rc;
       if (rc == OPMOS_OK) {
@@ -748,6 +823,7 @@ int opmos_solve_batch(const opmos_graph* g, uint32_t nq, const uint32_t* starts,
   }
   return OPMOS_OK;
 }
+
 
 uint32_t opmos_result_count(const opmos_result* r) { return r ? r->count : 0; }
 uint32_t opmos_result_d(const opmos_result* r) { return r ? r->d : 0; }

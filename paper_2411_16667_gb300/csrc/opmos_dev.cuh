@@ -45,6 +45,7 @@ enum StatIdx {
   S_TEXPAND,  // phase 2
   S_TMERGE,   // phase 4
   S_TOUT,     // output
+  S_GOALINS,  // goal labels accepted into P during the search (P log length)
   kNStat
 };
 

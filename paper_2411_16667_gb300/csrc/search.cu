@@ -156,8 +156,10 @@ struct Search {
   }
 
   // ---------------- initialisation (Algorithm 1 l.1-4) ----------------
+  // Empty frontiers and histograms (Alg. 1 l.1-2). The team must pass a
+  // barrier before init_seed writes the start node's frontier.
   template <class Team>
-  __device__ void init(const Team& T, bool reset_ctl) {
+  __device__ void init_zero(const Team& T) {
     for (unsigned v = T.tid(); v < G.n; v += T.nthreads()) {
       A.fcount[v] = 0;
       A.fcap[v] = 0;
@@ -165,6 +167,11 @@ struct Search {
       A.node_head[v] = kNil;
     }
     for (unsigned i = T.tid(); i < 2u * kNB; i += T.nthreads()) A.hist[i] = 0;
+  }
+
+  // l_s = (v_s, 0) into OPEN and G_OP(v_s) (Alg. 1 l.3-4), control block reset.
+  template <class Team>
+  __device__ void init_seed(const Team& T, bool reset_ctl) {
     if (T.leader()) {
       if (reset_ctl) {
         C->error = 0;
@@ -826,14 +833,20 @@ struct Search {
   }
 
   // ---------------- output: P without dominated members, sorted, with paths ----------------
+  // Four parts separated by team barriers (single query) or by iterations of
+  // the multi-query kernel: filter | rank | scan | paths. Regions of the
+  // output pool: res_off holds k'*D costs then k'+1 path offsets; res_path
+  // holds the path nodes then their arcs.
+
+  // (1) Prune(P, l) deferred from the search: drop members another member
+  // dominates; C->res_count must be 0 beforehand.
   template <class Team>
-  __device__ bool output(const Team& T) {
+  __device__ void out_filter(const Team& T) {
     const uint32_t t = P.goal;
     const unsigned k = A.fcount[t];
     const uint64_t fb = A.fbase[t];
     const unsigned cap = A.fcap[t];
-    const bool paths = !(P.flags & OPMOS_FLAG_NO_PATHS);
-    // (1) Prune(P, l) deferred from the search: drop members another member dominates
+    unsigned kept = 0;
     for (unsigned i = T.tid(); i < k; i += T.nthreads()) {
       uint32_t ci[D];
 #pragma unroll
@@ -849,19 +862,32 @@ struct Search {
         A.lstatus[A.fpool[fb + (size_t)D * cap + i]] = ST_DEAD;
         st[S_PRUNED]++;
       } else {
-        atomicAdd(&C->res_count, 1u);
+        ++kept;
       }
     }
-    if (!T.sync(C)) return false;
-    // (2) region 1: costs (k'*D, lexicographic) then path offsets (k'+1)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    if (lane_id() == 0 && kept) atomicAdd(&C->res_count, kept);
+  }
+
+  // (2a) region 1 allocation, one thread.
+  __device__ void out_alloc1() {
     const unsigned kk_live = ld_volatile(&C->res_count);
-    if (T.leader()) {
-      const unsigned long long words = (unsigned long long)kk_live * D + kk_live + 1;
-      const unsigned long long off = atomicAdd(O.used, words);
-      if (off + words > O.cap) set_error(C, OPMOS_ERR_CAPACITY);
-      C->res_off = off;
-    }
-    if (!T.sync(C)) return false;
+    const unsigned long long words = (unsigned long long)kk_live * D + kk_live + 1;
+    const unsigned long long off = atomicAdd(O.used, words);
+    if (off + words > O.cap) set_error(C, OPMOS_ERR_CAPACITY);
+    C->res_off = off;
+  }
+
+  // (2b) lexicographic rank of every kept member; costs and path lengths.
+  template <class Team>
+  __device__ void out_rank(const Team& T) {
+    const uint32_t t = P.goal;
+    const unsigned k = A.fcount[t];
+    const uint64_t fb = A.fbase[t];
+    const unsigned cap = A.fcap[t];
+    const bool paths = !(P.flags & OPMOS_FLAG_NO_PATHS);
+    const unsigned kk_live = ld_volatile(&C->res_count);
     const unsigned long long off = C->res_off;
     for (unsigned i = T.tid(); i < k; i += T.nthreads()) {
       const uint32_t idi = A.fpool[fb + (size_t)D * cap + i];
@@ -878,6 +904,10 @@ struct Search {
             A.lstatus[A.fpool[fb + (size_t)D * cap + j]] != ST_DEAD)
           ++rank;
       }
+      if (rank >= kk_live || off + (unsigned long long)kk_live * D + kk_live + 1 > O.cap) {
+        set_error(C, OPMOS_ERR_CAPACITY);  // never write outside the allocated region
+        continue;
+      }
 #pragma unroll
       for (int kk = 0; kk < D; ++kk) O.words[off + (size_t)rank * D + kk] = ci[kk];
       unsigned len = 0;
@@ -886,49 +916,75 @@ struct Search {
       O.words[off + (size_t)kk_live * D + rank] = len;
       A.lpver[idi] = rank;  // remembered for the path pass
     }
-    if (!T.sync(C)) return false;
-    // (3) exclusive scan of path lengths by the leader block, then region 2
-    if (T.leader_block()) {
-      uint32_t* lens = O.words + off + (size_t)kk_live * D;
-      unsigned carry = 0;
-      for (unsigned b0 = 0; b0 < kk_live + 1; b0 += blockDim.x) {
-        const unsigned i = b0 + threadIdx.x;
-        const unsigned x = i < kk_live ? lens[i] : 0;
-        unsigned total;
-        const unsigned ex = block_exclusive_scan(x, S.warp, total);
-        if (i <= kk_live) lens[i] = carry + ex;
-        carry += total;
+  }
+
+  // (3) exclusive scan of the path lengths and region 2 allocation; one block.
+  __device__ void out_scan() {
+    const bool paths = !(P.flags & OPMOS_FLAG_NO_PATHS);
+    const unsigned kk_live = ld_volatile(&C->res_count);
+    const unsigned long long off = C->res_off;
+    uint32_t* lens = O.words + off + (size_t)kk_live * D;
+    unsigned carry = 0;
+    for (unsigned b0 = 0; b0 < kk_live + 1; b0 += blockDim.x) {
+      const unsigned i = b0 + threadIdx.x;
+      const unsigned x = i < kk_live ? lens[i] : 0;
+      unsigned total;
+      const unsigned ex = block_exclusive_scan(x, S.warp, total);
+      if (i <= kk_live) lens[i] = carry + ex;
+      carry += total;
+    }
+    if (threadIdx.x == 0) {
+      const unsigned long long total = carry;
+      const unsigned long long words = paths ? 2 * total - kk_live : 0;
+      unsigned long long p0 = 0;
+      if (words) {
+        p0 = atomicAdd(O.used, words);
+        if (p0 + words > O.cap) set_error(C, OPMOS_ERR_CAPACITY);
       }
-      if (threadIdx.x == 0) {
-        const unsigned long long total = carry;
-        const unsigned long long words = paths ? 2 * total - kk_live : 0;
-        unsigned long long p0 = 0;
-        if (words) {
-          p0 = atomicAdd(O.used, words);
-          if (p0 + words > O.cap) set_error(C, OPMOS_ERR_CAPACITY);
-        }
-        C->res_path = p0;
-        C->res_total = total;
+      C->res_path = p0;
+      C->res_total = total;
+    }
+  }
+
+  // (4) parent-chain walks: nodes start..goal and the arcs between them.
+  template <class Team>
+  __device__ void out_paths(const Team& T) {
+    if (P.flags & OPMOS_FLAG_NO_PATHS) return;
+    const uint32_t t = P.goal;
+    const unsigned k = A.fcount[t];
+    const uint64_t fb = A.fbase[t];
+    const unsigned cap = A.fcap[t];
+    const unsigned kk_live = ld_volatile(&C->res_count);
+    const unsigned long long off = C->res_off, p0 = C->res_path, total = C->res_total;
+    const uint32_t* offs = O.words + off + (size_t)kk_live * D;
+    if (p0 + 2 * total > O.cap + kk_live) return;  // region 2 was not granted
+    for (unsigned i = T.tid(); i < k; i += T.nthreads()) {
+      const uint32_t idi = A.fpool[fb + (size_t)D * cap + i];
+      if (A.lstatus[idi] == ST_DEAD) continue;
+      const unsigned rank = A.lpver[idi];
+      if (rank >= kk_live) continue;
+      const unsigned a = offs[rank], b = offs[rank + 1];
+      // nodes at p0 + [a, b); arcs at p0 + total + [a - rank, b - rank - 1)
+      unsigned pos = b;
+      for (uint32_t x = idi; x != kInf && pos > a; x = A.lparent[x]) {
+        --pos;
+        O.words[p0 + pos] = A.lnode[x];
+        if (A.lparent[x] != kInf) O.words[p0 + total + pos - rank - 1] = A.ledge[x];
       }
     }
+  }
+
+  template <class Team>
+  __device__ bool output(const Team& T) {
+    out_filter(T);
     if (!T.sync(C)) return false;
-    if (paths) {
-      const unsigned long long p0 = C->res_path, total = C->res_total;
-      const uint32_t* offs = O.words + off + (size_t)kk_live * D;
-      for (unsigned i = T.tid(); i < k; i += T.nthreads()) {
-        const uint32_t idi = A.fpool[fb + (size_t)D * cap + i];
-        if (A.lstatus[idi] == ST_DEAD) continue;
-        const unsigned rank = A.lpver[idi];
-        const unsigned a = offs[rank], b = offs[rank + 1];
-        // nodes at p0 + [a, b); arcs at p0 + total + [a - rank, b - rank - 1)
-        unsigned pos = b;
-        for (uint32_t x = idi; x != kInf && pos > a; x = A.lparent[x]) {
-          --pos;
-          O.words[p0 + pos] = A.lnode[x];
-          if (A.lparent[x] != kInf) O.words[p0 + total + pos - rank - 1] = A.ledge[x];
-        }
-      }
-    }
+    if (T.leader()) out_alloc1();
+    if (!T.sync(C)) return false;
+    out_rank(T);
+    if (!T.sync(C)) return false;
+    if (T.leader_block()) out_scan();
+    if (!T.sync(C)) return false;
+    out_paths(T);
     return true;
   }
 };
@@ -940,8 +996,11 @@ __device__ void run_query(const GraphDev& G, const QArena& A, QCtl* C, const QPa
                           const OutPool& O, const Team& T, QResult* R, bool reset_ctl) {
   __shared__ Shared S;
   Search<D> X(G, A, C, P, O, S);
-  X.init(T, reset_ctl);
+  X.init_zero(T);
+  if (reset_ctl && T.leader()) C->error = 0;
   bool ok = T.sync(C);
+  X.init_seed(T, reset_ctl);
+  ok = ok && T.sync(C);
   unsigned step = 0;
   unsigned long long tph = globaltimer();
   auto lap = [&](int idx) {
@@ -981,6 +1040,7 @@ __device__ void run_query(const GraphDev& G, const QArena& A, QCtl* C, const QPa
     lap(S_TOUT);
   }
   X.st[S_STEPS] = T.leader() ? step : 0;
+  X.st[S_GOALINS] = T.leader() ? ld_volatile(&C->plog_len) : 0;
   flush_stats<Team>(C, X.st);
   T.sync(C);
   if (T.leader()) {
@@ -1002,26 +1062,291 @@ __global__ void __launch_bounds__(kGridThreads, 1) search_grid_kernel(GraphDev G
   run_query<D>(G, A, C, P, O, GridTeam{}, R, false);
 }
 
+// ---------------------------------------------------------------------------
+// Multi-query persistent kernel (batch and serving): continuous batching of
+// many independent queries. Every iteration:
+//   P0  block 0 retires finished slots and admits queued queries into free
+//       slots (FREE -> INIT -> RUN -> OUT -> FREE);
+//   P1  INIT slots are initialised, OUT slots write their result, RUN slots
+//       build their OPEN histogram;
+//   P2  RUN slots extract and expand;  P3  RUN slots merge.
+// In P1-P3 each block derives the same assignment of "virtual blocks" to slots
+// (a running slot gets a share of the grid in proportion to its work, at
+// least one block), so large and small queries advance side by side.
+// ---------------------------------------------------------------------------
+struct SubTeam {
+  unsigned j, nb;
+  __device__ __forceinline__ unsigned tid() const { return j * blockDim.x + threadIdx.x; }
+  __device__ __forceinline__ unsigned nthreads() const { return nb * blockDim.x; }
+  __device__ __forceinline__ unsigned wid() const { return tid() >> 5; }
+  __device__ __forceinline__ unsigned nwarps() const { return nthreads() >> 5; }
+  __device__ __forceinline__ bool leader_block() const { return j == 0; }
+  __device__ __forceinline__ bool leader() const { return j == 0 && threadIdx.x == 0; }
+};
+
+__device__ bool mq_barrier(MCtl* M) {
+  __shared__ unsigned s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned gen = ld_volatile(&M->bar_gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(&M->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&M->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&M->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer();
+      unsigned spins = 0;
+      while (ld_volatile(&M->bar_gen) == gen) {
+        if (++spins > 64) __nanosleep(64);
+        if ((spins & 255u) == 0) {
+          if (ld_volatile(&M->error) != 0) break;
+          if (globaltimer() - t0 > kBarrierTimeoutNs) {
+            atomicCAS(&M->error, 0u, (unsigned)OPMOS_ERR_TIMEOUT);
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ld_volatile(&M->error) == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// P0: slot transitions and admission (block 0).
+__device__ void mq_write_result(const MSlot& sl, QCtl* C, QResult* results) {
+  QResult* R = &results[sl.qidx];
+  R->status = ld_volatile(&C->error);
+  R->count = C->res_count;
+  R->off = C->res_off;
+  R->path = C->res_path;
+  R->total = C->res_total;
+  R->labels = C->n_labels;
+  R->f_words = C->f_words;
+  C->stats[S_STEPS] = C->step;
+  C->stats[S_GOALINS] = C->plog_len;
+  for (int i = 0; i < kNStat; ++i) R->stats[i] = C->stats[i];
+}
+
+__device__ void mq_alloc_region1(const MSlot& sl, QCtl* C, const OutPool& O) {
+  const unsigned kk_live = ld_volatile(&C->res_count);
+  const unsigned long long words = (unsigned long long)kk_live * sl.d + kk_live + 1;
+  const unsigned long long off = atomicAdd(O.used, words);
+  if (off + words > O.cap) atomicCAS(&C->error, 0u, (unsigned)OPMOS_ERR_CAPACITY);
+  C->res_off = off;
+}
+
+__device__ void mq_schedule(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue,
+                            const unsigned* q_count_ptr, const GraphDev* graphs, MCtl* M, QResult* results,
+                            const OutPool& O) {
+  __shared__ unsigned s_busy;
+  if (threadIdx.x == 0) s_busy = 0;
+  __syncthreads();
+  const unsigned q_count = ld_volatile(q_count_ptr);
+  for (unsigned q = threadIdx.x; q < nslots; q += blockDim.x) {
+    MSlot& sl = slots[q];
+    QCtl* C = &ctls[q];
+    unsigned st = sl.state;
+    if (st == SL_RUN) {
+      const unsigned step = C->step + 1;
+      C->step = step;
+      if (ld_volatile(&C->error) || ld_volatile(&C->open_count[step & 1u]) == 0)
+        st = SL_OUT1;
+      else if (globaltimer() - C->t_start > sl.P.time_limit_ns) {
+        atomicCAS(&C->error, 0u, (unsigned)OPMOS_ERR_TIMEOUT);
+        st = SL_OUT1;
+      }
+      if (st == SL_OUT1) C->res_count = 0;
+    } else if (st == SL_INIT) {
+      st = (ld_volatile(&C->error) || ld_volatile(&C->open_count[0]) == 0) ? SL_OUT1 : SL_RUN;
+      if (st == SL_OUT1) C->res_count = 0;
+    } else if (st == SL_OUT1 || st == SL_OUT2 || st == SL_OUT3 || st == SL_OUT4) {
+      // one output part per iteration; an error ends the output early
+      if (ld_volatile(&C->error) || st == SL_OUT4) {
+        mq_write_result(sl, C, results);
+        st = SL_FREE;
+      } else if (st == SL_OUT1) {
+        mq_alloc_region1(sl, C, O);
+        if (ld_volatile(&C->error)) {  // no room for the result: report, never write
+          mq_write_result(sl, C, results);
+          st = SL_FREE;
+        } else {
+          st = SL_OUT2;
+        }
+      } else {
+        st = st + 1;
+      }
+    }
+    if (st == SL_FREE) {
+      unsigned qn = ld_volatile(&M->q_next);
+      while (qn < q_count) {
+        const unsigned got = atomicCAS(&M->q_next, qn, qn + 1);
+        if (got == qn) break;
+        qn = got;
+      }
+      if (qn < q_count) {
+        const MQuery Q = queue[qn];
+        sl.P.start = Q.start;
+        sl.P.goal = Q.goal;
+        sl.P.h = Q.h;
+        sl.G = graphs[Q.graph];
+        sl.d = Q.d;
+        sl.qidx = qn;
+        st = SL_INIT;
+      }
+    }
+    sl.state = st;
+    if (st != SL_FREE) atomicAdd(&s_busy, 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    M->iter++;
+    if (s_busy == 0 && ld_volatile(&M->q_next) >= ld_volatile(q_count_ptr) && ld_volatile(&M->closing))
+      M->done = 1;
+  }
+}
+
 template <int D>
-__global__ void __launch_bounds__(256) search_batch_kernel(GraphDev G, const QArena* arenas, QCtl* ctls,
-                                                           const BatchQuery* qs, unsigned nq,
-                                                           unsigned* next_q, QParams base, OutPool O,
-                                                           QResult* results) {
-  __shared__ unsigned s_q;
-  const QArena A = arenas[blockIdx.x];
-  QCtl* C = &ctls[blockIdx.x];
+__device__ void mq_work(MSlot* slots, QCtl* ctls, unsigned q, unsigned j, unsigned nb, unsigned ph,
+                        const OutPool& O, QResult* results, Shared& S) {
+  const QArena A = slots[q].A;
+  const QParams P = slots[q].P;
+  const GraphDev G = slots[q].G;
+  const unsigned st = slots[q].state;
+  QCtl* C = &ctls[q];
+  Search<D> X(G, A, C, P, O, S);
+  if (st == SL_INIT) {
+    const BlockTeam T;
+    X.init_zero(T);
+    if (threadIdx.x == 0) C->error = 0;
+    __syncthreads();
+    X.init_seed(T, true);
+    __syncthreads();
+    flush_stats<BlockTeam>(C, X.st);
+  } else if (st == SL_OUT1) {
+    X.out_filter(SubTeam{j, nb});
+    flush_stats<SubTeam>(C, X.st);
+  } else if (st == SL_OUT2) {
+    X.out_rank(SubTeam{j, nb});
+  } else if (st == SL_OUT3) {
+    X.out_scan();
+  } else if (st == SL_OUT4) {
+    X.out_paths(SubTeam{j, nb});
+  } else if (st == SL_RUN) {
+    const SubTeam T{j, nb};
+    const unsigned cur = C->step & 1u;
+    const unsigned n_in = ld_volatile(&C->open_count[cur]);
+    const unsigned long long base = ld_volatile64(&C->min_key[cur]);
+    BinParams bp;
+    bp.b0 = (uint32_t)(base >> 32);
+    bp.b1 = (uint32_t)base;
+    bp.delta = P.delta;
+    bp.s1 = 0;
+    for (unsigned sp = ld_volatile(&C->f1span[cur]); (sp >> bp.s1) >= (unsigned)kNB1; ++bp.s1) {
+    }
+    if (ph == 1)
+      X.phase_hist(T, cur, n_in, bp);
+    else if (ph == 2)
+      X.phase_extract_expand(T, cur, n_in, bp);
+    else
+      X.phase_merge(T, cur);
+    flush_stats<SubTeam>(C, X.st);
+  }
+}
+
+__device__ __forceinline__ unsigned A_fcount_goal(const MSlot& sl) { return sl.A.fcount[sl.P.goal]; }
+
+// Work units of a slot in phase ph (0: none). INIT and the scan part of the
+// output get one block; the other output parts a share like search phases.
+__device__ __forceinline__ unsigned mq_weight(const MSlot& sl, QCtl* C, unsigned ph, bool& single) {
+  single = false;
+  const unsigned st = sl.state;
+  if (st == SL_FREE) return 0;
+  if (st == SL_INIT || st == SL_OUT3) {
+    single = ph == 1;
+    return ph == 1 ? 1u : 0u;
+  }
+  if (st >= SL_OUT1) return ph == 1 ? max(1u, ld_volatile(&C->res_count) + A_fcount_goal(sl)) : 0u;
+  const unsigned cur = C->step & 1u;
+  const unsigned w = ph == 3 ? ld_volatile(&C->touched_count) : ld_volatile(&C->open_count[cur]);
+  return w ? w : 1u;  // a running slot always gets a block (index builds run in every phase)
+}
+
+__device__ void mq_phase(unsigned ph, MSlot* slots, QCtl* ctls, unsigned nslots, const OutPool& O,
+                         QResult* results, Shared& S, unsigned* s_pref) {
+  // total weight of the multi-block slots
+  __shared__ unsigned long long s_wtot;
+  if (threadIdx.x == 0) s_wtot = 0;
+  __syncthreads();
+  unsigned long long wloc = 0;
+  for (unsigned q = threadIdx.x; q < nslots; q += blockDim.x) {
+    bool single;
+    const unsigned w = mq_weight(slots[q], &ctls[q], ph, single);
+    if (!single) wloc += w;
+  }
+  atomicAdd(&s_wtot, wloc);
+  __syncthreads();
+  const unsigned long long wtot = s_wtot > 0 ? s_wtot : 1;
+  const unsigned B = gridDim.x;
+  // virtual blocks per slot, then their prefix sums (chunked block scan)
+  unsigned carry = 0;
+  for (unsigned c0 = 0; c0 < nslots; c0 += blockDim.x) {
+    const unsigned q = c0 + threadIdx.x;
+    unsigned nbq = 0;
+    if (q < nslots) {
+      bool single;
+      const unsigned w = mq_weight(slots[q], &ctls[q], ph, single);
+      if (single)
+        nbq = 1;
+      else if (w)
+        nbq = (unsigned)min((unsigned long long)B, max(1ull, (w * (unsigned long long)B + wtot - 1) / wtot));
+    }
+    unsigned total;
+    const unsigned ex = block_exclusive_scan(nbq, S.warp, total);
+    if (q < nslots) s_pref[q] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) s_pref[nslots] = carry;
+  __syncthreads();
+  const unsigned VB = s_pref[nslots];
+  for (unsigned v = blockIdx.x; v < VB; v += B) {
+    unsigned lo = 0, hi = nslots;  // last q with s_pref[q] <= v
+    while (hi - lo > 1) {
+      const unsigned mid = (lo + hi) / 2;
+      if (s_pref[mid] <= v) lo = mid; else hi = mid;
+    }
+    const unsigned q = lo;
+    const unsigned j = v - s_pref[q], nb = s_pref[q + 1] - s_pref[q];
+    switch (slots[q].d) {
+#define MQ_CASE(DD) \
+  case DD:          \
+    mq_work<DD>(slots, ctls, q, j, nb, ph, O, results, S); \
+    break;
+      MQ_CASE(1) MQ_CASE(2) MQ_CASE(3) MQ_CASE(4) MQ_CASE(5) MQ_CASE(6) MQ_CASE(7) MQ_CASE(8)
+#undef MQ_CASE
+      default:
+        break;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kMultiThreads, 2)
+    multi_kernel(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue, const unsigned* q_count_ptr,
+                 const GraphDev* graphs, OutPool O, QResult* results, MCtl* M) {
+  __shared__ Shared S;
+  __shared__ unsigned s_pref[kMaxSlots + 1];
   for (;;) {
-    if (threadIdx.x == 0) s_q = atomicAdd(next_q, 1u);
-    __syncthreads();
-    const unsigned q = s_q;
-    __syncthreads();
-    if (q >= nq) break;
-    QParams P = base;
-    P.start = qs[q].start;
-    P.goal = qs[q].goal;
-    P.h = qs[q].h;
-    run_query<D>(G, A, C, P, O, BlockTeam{}, &results[q], true);
-    __syncthreads();
+    if (blockIdx.x == 0) mq_schedule(slots, ctls, nslots, queue, q_count_ptr, graphs, M, results, O);
+    if (!mq_barrier(M)) return;
+    if (ld_volatile(&M->done)) return;
+    for (unsigned ph = 1; ph <= 3; ++ph) {
+      mq_phase(ph, slots, ctls, nslots, O, results, S, s_pref);
+      if (!mq_barrier(M)) return;
+    }
   }
 }
 
@@ -1036,20 +1361,9 @@ static cudaError_t launch_grid_d(const GraphDev& G, const QArena& A, QCtl* C, co
 }
 
 template <int D>
-static cudaError_t launch_batch_d(const GraphDev& G, const QArena* arenas, QCtl* ctls, const BatchQuery* qs,
-                                  unsigned nq, unsigned* next_q, const QParams& P, const OutPool& O,
-                                  QResult* R, unsigned blocks, cudaStream_t s) {
-  search_batch_kernel<D><<<blocks, 256, 0, s>>>(G, arenas, ctls, qs, nq, next_q, P, O, R);
-  return cudaGetLastError();
-}
-
-template <int D>
-static int occupancy_d(int which) {
+static int occupancy_d(int) {
   int nb = 0;
-  if (which == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_grid_kernel<D>, kGridThreads, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_batch_kernel<D>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_grid_kernel<D>, kGridThreads, 0);
   return nb;
 }
 
@@ -1074,13 +1388,18 @@ cudaError_t launch_search_grid(unsigned d, const GraphDev& G, const QArena& A, Q
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_search_batch(unsigned d, const GraphDev& G, const QArena* arenas, QCtl* ctls,
-                                const BatchQuery* qs, unsigned nq, unsigned* next_q, const QParams& P,
-                                const OutPool& O, QResult* R, unsigned blocks, cudaStream_t s) {
-#define CALL(D) launch_batch_d<D>(G, arenas, ctls, qs, nq, next_q, P, O, R, blocks, s)
-  OPMOS_DISPATCH_D(d, CALL)
-#undef CALL
-  return cudaErrorInvalidValue;
+cudaError_t launch_multi(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue,
+                         const unsigned* q_count_ptr, const GraphDev* graphs, const OutPool& O, QResult* results,
+                         MCtl* M, unsigned blocks, cudaStream_t s) {
+  void* args[] = {(void*)&slots, (void*)&ctls, (void*)&nslots, (void*)&queue, (void*)&q_count_ptr,
+                  (void*)&graphs, (void*)&O, (void*)&results, (void*)&M};
+  return cudaLaunchCooperativeKernel((void*)multi_kernel, dim3(blocks), dim3(kMultiThreads), args, 0, s);
+}
+
+int multi_occupancy() {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, multi_kernel, kMultiThreads, 0);
+  return nb;
 }
 
 int search_occupancy(unsigned d, int batch) {

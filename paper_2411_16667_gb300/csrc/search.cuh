@@ -5,9 +5,26 @@
 
 namespace opmos {
 
-struct BatchQuery {
-  uint32_t start, goal;
-  const uint32_t* h;  // d * n heuristic toward goal
+// Multi-query kernel (batch and serving) --------------------------------------
+constexpr unsigned kMultiThreads = 256;  // threads per block
+constexpr unsigned kMaxSlots = 1024;     // concurrent queries
+enum SlotState : unsigned { SL_FREE = 0, SL_INIT = 1, SL_RUN = 2, SL_OUT1 = 3, SL_OUT2 = 4, SL_OUT3 = 5, SL_OUT4 = 6 };
+
+struct MSlot {     // one concurrent query: its arena and current parameters
+  QArena A;
+  QParams P;
+  GraphDev G;
+  unsigned d, state, qidx, pad;
+};
+
+struct MQuery {    // a queued query
+  uint32_t graph, start, goal, d;
+  const uint32_t* h;  // d * n heuristic toward goal (device)
+};
+
+struct MCtl {      // grid-wide control of the multi-query kernel
+  unsigned bar_count, bar_gen, error, done;
+  unsigned q_next, closing, iter, pad;
 };
 
 // Result descriptor of one query, written by the team leader at the end.
@@ -26,10 +43,11 @@ struct QResult {
 
 cudaError_t launch_search_grid(unsigned d, const GraphDev& G, const QArena& A, QCtl* C, const QParams& P,
                                const OutPool& O, QResult* R, unsigned blocks, cudaStream_t s);
-cudaError_t launch_search_batch(unsigned d, const GraphDev& G, const QArena* arenas, QCtl* ctls,
-                                const BatchQuery* qs, unsigned nq, unsigned* next_q, const QParams& P,
-                                const OutPool& O, QResult* R, unsigned blocks, cudaStream_t s);
 int search_occupancy(unsigned d, int batch);
+cudaError_t launch_multi(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue,
+                         const unsigned* q_count_ptr, const GraphDev* graphs, const OutPool& O, QResult* results,
+                         MCtl* M, unsigned blocks, cudaStream_t s);
+int multi_occupancy();
 
 // Ideal-point heuristic jobs: h_out[v] = shortest v->goal distance under
 // objective k (Sec. 4), one thread block per job.

@@ -44,7 +44,7 @@ class Stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in (
         "extracted", "dead_skipped", "goal_pruned", "candidates", "inserted", "pruned", "steps",
         "frontier_cmp", "p_cmp", "bytes", "heuristic_ns", "search_ns", "total_ns")] + [
-        ("phase_ns", ctypes.c_uint64 * 4)]
+        ("phase_ns", ctypes.c_uint64 * 4), ("goal_inserted", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         d = {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "phase_ns"}
@@ -213,9 +213,19 @@ def _take(res) -> Result:
         L.opmos_result_free(res)
 
 
+def _options(**kw) -> Options:
+    """Options with only the given fields set; zero fields take the library
+    default of the call they are passed to (single query or batch)."""
+    o = Options()
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
 def opmos_solve(graph: opmos_graph, start: int, goal: int, heur: opmos_heur | None = None,
                 options: Options | None = None, **kw) -> Result:
-    o = options or opmos_default_options(**kw)
+    o = options or _options(**kw)
     res = ctypes.c_void_p()
     _check(lib().opmos_solve(graph.handle, heur.handle if heur else None, start, goal, ctypes.byref(o),
                              ctypes.byref(res)), "opmos_solve")
@@ -227,7 +237,7 @@ def opmos_solve_batch(graph: opmos_graph, starts, goals, options: Options | None
     starts = np.ascontiguousarray(starts, np.uint32)
     goals = np.ascontiguousarray(goals, np.uint32)
     nq = int(starts.shape[0])
-    o = options or opmos_default_options(**kw)
+    o = options or _options(**kw)
     outs = (ctypes.c_void_p * max(nq, 1))()
     status = np.zeros(max(nq, 1), np.int32)
     _check(lib().opmos_solve_batch(graph.handle, nq, _ptr(starts), _ptr(goals), ctypes.byref(o),
