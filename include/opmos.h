@@ -191,8 +191,16 @@ OPMOS_API void opmos_result_free(opmos_result* r);
 
 /* Continuous-batching server over device-resident graphs. Queries submitted
  * while others run are admitted as soon as a slot and the device memory
- * budget (opt->mem_budget_bytes, default 64 GiB) allow; admitted queries run
- * concurrently in one persistent kernel that polls a device mailbox. */
+ * budget (opt->mem_budget_bytes, default 64 GiB; one slot = a 512 MiB search
+ * arena + a 32 MiB result pool) allow; admitted queries run concurrently in
+ * one persistent kernel that reads a queue in host-mapped memory, and each
+ * result stays in its slot until opmos_server_poll collects it. submit
+ * computes the query's heuristic on the SMs the resident kernel leaves free;
+ * it fails with OPMOS_ERR_CAPACITY when 2 x slots queries are outstanding.
+ * While a server exists, do not call the other compute entry points or
+ * device-wide synchronising CUDA calls (cudaFree, cudaDeviceSynchronize) on
+ * the same device: they wait for the resident kernel. A query whose arena
+ * overflows reports OPMOS_ERR_CAPACITY (no retry). */
 OPMOS_API int opmos_server_create(const opmos_graph* const* graphs, uint32_t ngraphs,
                         const opmos_options* opt, opmos_server** out);
 /* d = number of leading objectives to use (0 = all). *ticket identifies it. */

@@ -8,8 +8,10 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <atomic>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "opmos.h"
@@ -520,12 +522,12 @@ int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const st
   // query that finds it full is reported as a capacity overflow and re-run
   const size_t out_words = std::max<size_t>(kOutWords, std::min<size_t>((size_t)nq << 18, 1ull << 30));
   void* outp = nullptr;
-  const size_t misc_bytes = slots * (sizeof(MSlot) + sizeof(QCtl)) + nq * (sizeof(MQuery) + sizeof(QResult)) +
+  const size_t misc_bytes = slots * (sizeof(MSlot) + sizeof(QCtl) + 4) + nq * (sizeof(MQuery) + sizeof(QResult)) +
                             sizeof(GraphDev) + sizeof(MCtl) + 16 * 256;
   if (int rc = g_out.get(out_words * 4 + misc_bytes, &outp)) return rc;
   char* op = (char*)outp;
   unsigned long long* used = carve<unsigned long long>(op, 1);
-  unsigned* qcount = carve<unsigned>(op, 1);
+  unsigned* hctl = carve<unsigned>(op, HC_RELEASE + slots);
   MCtl* M = carve<MCtl>(op, 1);
   GraphDev* dgraphs = carve<GraphDev>(op, 1);
   QCtl* ctls = carve<QCtl>(op, slots);
@@ -533,22 +535,26 @@ int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const st
   MQuery* dqs = carve<MQuery>(op, nq);
   QResult* dres = carve<QResult>(op, nq);
   uint32_t* words = carve<uint32_t>(op, out_words);
+  for (auto& sl : hslots) sl.O = OutPool{words, out_words, used};  // one pool shared by all slots
   MCtl hM{};
-  hM.closing = 1;  // every query is queued up front
+  hM.qcap = nq;
+  hM.hold = 0;
+  std::vector<unsigned> hc(HC_RELEASE + slots, 0);
+  hc[HC_TAIL] = nq;     // every query is queued up front
+  hc[HC_CLOSING] = 1;   // and no more will come
   CK(cudaMemsetAsync(used, 0, 8, s));
-  CK(cudaMemcpyAsync(qcount, &nq, 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(hctl, hc.data(), hc.size() * 4, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(M, &hM, sizeof(MCtl), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dgraphs, &g->dev, sizeof(GraphDev), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(ctls, 0, slots * sizeof(QCtl), s));
   CK(cudaMemsetAsync(dres, 0, nq * sizeof(QResult), s));
   CK(cudaMemcpyAsync(dslots, hslots.data(), slots * sizeof(MSlot), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(dqs, qs.data(), nq * sizeof(MQuery), cudaMemcpyHostToDevice, s));
-  OutPool O{words, out_words, used};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
-  cudaError_t e = launch_multi(dslots, ctls, slots, dqs, qcount, dgraphs, O, dres, M, blocks, s);
+  cudaError_t e = launch_multi(dslots, ctls, slots, dqs, hctl, dgraphs, dres, nullptr, M, blocks, s);
   cudaEventRecord(e1, s);
   std::vector<QResult> hres(nq);
   MCtl hM2{};
@@ -855,5 +861,276 @@ int opmos_result_stats(const opmos_result* r, opmos_stats* out) {
 }
 
 void opmos_result_free(opmos_result* r) { delete r; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Continuous-batching server: one persistent multi-query kernel stays
+// resident; queries are queued through host-mapped memory and admitted as
+// slots (arena + result pool, within the memory budget) free up; results are
+// kept in their slot until the host collects them.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kServeSlotBytes = 512ull << 20;   // search arena per slot
+constexpr size_t kServeOutWords = 8ull << 20;      // result pool per slot (32 MiB)
+constexpr unsigned kServeHeurBlocks = 16;          // heuristic blocks left room beside the kernel
+}  // namespace
+
+struct opmos_server {
+  std::mutex mu;
+  std::vector<const opmos_graph*> graphs;
+  opmos_graph shape{};  // largest n / degree, for arena planning
+  uint32_t dmax = 0;
+  unsigned nslots = 0, qcap = 0, blocks = 0;
+  opmos_options o{};
+  cudaStream_t kstream = nullptr, hstream = nullptr;
+  char* dmem = nullptr;
+  char* hmem = nullptr;
+  uint32_t* hring = nullptr;  // heuristics of queued/running queries, qcap x dmax x nmax
+  uint32_t* hscratch = nullptr;
+  HJob* djobs = nullptr;
+  unsigned* hkctr = nullptr;
+  std::vector<uint32_t*> pool_words;  // per slot, device
+  MQuery* hq = nullptr;               // host views of the mapped rings
+  QResult* hres = nullptr;
+  unsigned* hdone = nullptr;
+  unsigned* hctl = nullptr;
+  std::vector<uint8_t> inuse;
+  std::vector<uint32_t> qd;  // objectives of each ring entry
+  uint64_t next_ticket = 0;
+  bool running = false;
+};
+
+namespace {
+
+void server_free(opmos_server* sv) {
+  if (sv->running) {
+    *reinterpret_cast<volatile unsigned*>(&sv->hctl[HC_CLOSING]) = 2;  // stop now
+    for (unsigned i = 0; i < sv->nslots; ++i) *reinterpret_cast<volatile unsigned*>(&sv->hctl[HC_RELEASE + i]) = 1;
+    cudaStreamSynchronize(sv->kstream);
+  }
+  if (sv->dmem) cudaFree(sv->dmem);
+  if (sv->hmem) cudaFreeHost(sv->hmem);
+  if (sv->kstream) cudaStreamDestroy(sv->kstream);
+  if (sv->hstream) cudaStreamDestroy(sv->hstream);
+  delete sv;
+}
+
+}  // namespace
+
+extern "C" {
+
+int opmos_server_create(const opmos_graph* const* graphs, uint32_t ngraphs, const opmos_options* opt,
+                        opmos_server** out) {
+  if (!out) return fail(OPMOS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!graphs || ngraphs == 0) return fail(OPMOS_ERR_INVALID_ARG, "no graphs");
+  const DevInfo di = device_info();
+  if (!di.ok) return fail(OPMOS_ERR_CUDA, "no CUDA device");
+  auto* sv = new (std::nothrow) opmos_server;
+  if (!sv) return fail(OPMOS_ERR_OUT_OF_MEMORY, "host allocation");
+  opmos_options o = resolve(opt, true);
+  if (!opt || !opt->mem_budget_bytes) o.mem_budget_bytes = 64ull << 30;
+  sv->o = o;
+  for (uint32_t i = 0; i < ngraphs; ++i) {
+    if (!graphs[i]) {
+      delete sv;
+      return fail(OPMOS_ERR_INVALID_ARG, "graph %u is NULL", i);
+    }
+    sv->graphs.push_back(graphs[i]);
+    sv->shape.n = std::max(sv->shape.n, graphs[i]->n);
+    sv->shape.maxdeg = std::max(sv->shape.maxdeg, graphs[i]->maxdeg);
+    sv->dmax = std::max(sv->dmax, graphs[i]->d);
+  }
+  uint32_t Dchk;
+  {
+    opmos_options oc = o;
+    oc.d_used = 0;
+    opmos_graph tmp = sv->shape;
+    tmp.d = sv->dmax;
+    if (int rc = check_options(oc, &tmp, &Dchk)) {
+      delete sv;
+      return rc;
+    }
+  }
+  ArenaPlan pl;
+  if (int rc = plan_arena(&sv->shape, sv->dmax, o.window, kServeSlotBytes, true, &pl)) {
+    delete sv;
+    return rc;
+  }
+  const size_t slot_bytes = (pl.bytes + 255) / 256 * 256;
+  const size_t pool_bytes = kServeOutWords * 4 + 256;
+  const size_t per_slot = slot_bytes + pool_bytes;
+  sv->nslots = (unsigned)std::min<size_t>(kMaxSlots, std::max<size_t>(1, o.mem_budget_bytes / per_slot));
+  sv->qcap = std::max(64u, 2 * sv->nslots);
+  const size_t hstride = (size_t)sv->dmax * sv->shape.n;
+  const size_t spb = 5 * (size_t)sv->shape.n + 64;
+  const size_t misc = sizeof(MCtl) + sv->graphs.size() * sizeof(GraphDev) + sv->nslots * (sizeof(MSlot) + sizeof(QCtl)) +
+                      OPMOS_MAX_D * sizeof(HJob) + 64 + 32 * 256;
+  const size_t dbytes = sv->nslots * per_slot + sv->qcap * hstride * 4 + kServeHeurBlocks * spb * 4 + misc;
+  cudaError_t e = cudaMalloc(&sv->dmem, dbytes);
+  if (e != cudaSuccess) {
+    sv->dmem = nullptr;
+    server_free(sv);
+    return cuda_fail(e, "server device memory");
+  }
+  const size_t hbytes = sv->qcap * (sizeof(MQuery) + sizeof(QResult) + 4) + (HC_RELEASE + sv->nslots) * 4 + 8 * 256;
+  e = cudaHostAlloc(&sv->hmem, hbytes, cudaHostAllocMapped);
+  if (e != cudaSuccess) {
+    sv->hmem = nullptr;
+    server_free(sv);
+    return cuda_fail(e, "server mapped host memory");
+  }
+  std::memset(sv->hmem, 0, hbytes);
+  char* hp = sv->hmem;
+  sv->hq = carve<MQuery>(hp, sv->qcap);
+  sv->hres = carve<QResult>(hp, sv->qcap);
+  sv->hdone = carve<unsigned>(hp, sv->qcap);
+  sv->hctl = carve<unsigned>(hp, HC_RELEASE + sv->nslots);
+  auto dev_of = [&](void* h) {
+    void* d = nullptr;
+    cudaHostGetDevicePointer(&d, h, 0);
+    return d;
+  };
+  char* dp = sv->dmem;
+  MCtl* M = carve<MCtl>(dp, 1);
+  GraphDev* dgraphs = carve<GraphDev>(dp, sv->graphs.size());
+  QCtl* ctls = carve<QCtl>(dp, sv->nslots);
+  MSlot* dslots = carve<MSlot>(dp, sv->nslots);
+  sv->djobs = carve<HJob>(dp, OPMOS_MAX_D);
+  sv->hkctr = carve<unsigned>(dp, 16);
+  sv->hscratch = carve<uint32_t>(dp, kServeHeurBlocks * spb);
+  sv->hring = carve<uint32_t>(dp, sv->qcap * hstride);
+  std::vector<MSlot> hslots(sv->nslots);
+  for (unsigned i = 0; i < sv->nslots; ++i) {
+    char* base = carve<char>(dp, per_slot);
+    MSlot& sl = hslots[i];
+    std::memset(&sl, 0, sizeof(sl));
+    layout_arena(&sv->shape, sv->dmax, pl, base, &sl.A);
+    char* pp = base + slot_bytes;
+    unsigned long long* used = carve<unsigned long long>(pp, 1);
+    uint32_t* words = carve<uint32_t>(pp, kServeOutWords);
+    sl.O = OutPool{words, kServeOutWords, used};
+    sv->pool_words.push_back(words);
+    sl.P.window = o.window;
+    sl.P.lanes = o.lanes_per_label;
+    sl.P.delta = o.delta;
+    sl.P.tile = o.tile;
+    sl.P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, pl.label_cap);
+    sl.P.flags = o.flags;
+    sl.P.time_limit_ns = kTimeLimitNs;
+    sl.state = SL_FREE;
+  }
+  std::vector<GraphDev> gd;
+  for (auto* g : sv->graphs) gd.push_back(g->dev);
+  MCtl hM{};
+  hM.qcap = sv->qcap;
+  hM.hold = 1;
+  sv->inuse.assign(sv->qcap, 0);
+  sv->qd.assign(sv->qcap, 0);
+  e = cudaStreamCreateWithFlags(&sv->kstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->hstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemcpy(M, &hM, sizeof(MCtl), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dgraphs, gd.data(), gd.size() * sizeof(GraphDev), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(ctls, 0, sv->nslots * sizeof(QCtl));
+  if (e == cudaSuccess) e = cudaMemcpy(dslots, hslots.data(), sv->nslots * sizeof(MSlot), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    server_free(sv);
+    return cuda_fail(e, "server set-up");
+  }
+  const int occ = multi_occupancy();
+  const unsigned full = (unsigned)di.sms * (unsigned)std::min(occ, 2);
+  sv->blocks = full > 2 * kServeHeurBlocks ? full - 2 * kServeHeurBlocks : std::max(1u, full / 2);
+  e = launch_multi(dslots, ctls, sv->nslots, (MQuery*)dev_of(sv->hq), (unsigned*)dev_of(sv->hctl), dgraphs,
+                   (QResult*)dev_of(sv->hres), (unsigned*)dev_of(sv->hdone), M, sv->blocks, sv->kstream);
+  if (e != cudaSuccess) {
+    server_free(sv);
+    return cuda_fail(e, "server kernel launch");
+  }
+  sv->running = true;
+  *out = sv;
+  return OPMOS_OK;
+}
+
+int opmos_server_submit(opmos_server* sv, uint32_t graph, uint32_t d, uint32_t start, uint32_t goal,
+                        uint64_t* ticket) {
+  if (!sv || !ticket) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (graph >= sv->graphs.size()) return fail(OPMOS_ERR_INVALID_ARG, "graph %u out of range", graph);
+  const opmos_graph* g = sv->graphs[graph];
+  const uint32_t D = d ? d : g->d;
+  if (D < 1 || D > g->d) return fail(OPMOS_ERR_INVALID_ARG, "d %u not in [1, %u]", D, g->d);
+  if (start >= g->n || goal >= g->n) return fail(OPMOS_ERR_INVALID_ARG, "start/goal out of range");
+  const uint64_t t = sv->next_ticket;
+  const unsigned idx = (unsigned)(t % sv->qcap);
+  if (sv->inuse[idx]) return fail(OPMOS_ERR_CAPACITY, "server queue full (%u outstanding queries)", sv->qcap);
+  // the heuristic of this query, on the SMs the resident kernel leaves free
+  uint32_t* h = sv->hring + (size_t)idx * sv->dmax * sv->shape.n;
+  HJob jobs[OPMOS_MAX_D];
+  for (uint32_t k = 0; k < D; ++k) jobs[k] = HJob{goal, k, h + (size_t)k * g->n};
+  cudaStream_t s = sv->hstream;
+  CK(cudaMemsetAsync(sv->hkctr, 0, 2 * sizeof(unsigned), s));
+  CK(cudaMemcpyAsync(sv->djobs, jobs, D * sizeof(HJob), cudaMemcpyHostToDevice, s));
+  CK(launch_heuristic(g->dev, sv->djobs, D, sv->hscratch, 5 * (size_t)sv->shape.n + 64,
+                      std::min<unsigned>(D, kServeHeurBlocks), g->delta, sv->hkctr, sv->hkctr + 1, s));
+  unsigned herr = 0;
+  CK(cudaMemcpyAsync(&herr, sv->hkctr + 1, 4, cudaMemcpyDeviceToHost, s));
+  // bounded wait: the heuristic runs on SMs the resident kernel leaves free
+  const auto tw = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t q = cudaStreamQuery(s);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return cuda_fail(q, "server heuristic");
+    if (std::chrono::steady_clock::now() - tw > std::chrono::seconds(30))
+      return fail(OPMOS_ERR_TIMEOUT, "server heuristic did not finish within 30 s");
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  if (herr) return fail((int)herr, "heuristic kernel reported error %u", herr);
+  MQuery q{graph, start, goal, D, h};
+  sv->hq[idx] = q;
+  sv->hdone[idx] = 0;
+  sv->inuse[idx] = 1;
+  sv->qd[idx] = D;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  *reinterpret_cast<volatile unsigned*>(&sv->hctl[HC_TAIL]) = (unsigned)(t + 1);
+  sv->next_ticket = t + 1;
+  *ticket = t;
+  return OPMOS_OK;
+}
+
+int opmos_server_poll(opmos_server* sv, uint64_t ticket, opmos_result** out) {
+  if (!sv || !out) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  const unsigned idx = (unsigned)(ticket % sv->qcap);
+  if (ticket >= sv->next_ticket || !sv->inuse[idx]) return fail(OPMOS_ERR_INVALID_ARG, "unknown ticket");
+  if (!*reinterpret_cast<volatile unsigned*>(&sv->hdone[idx])) return OPMOS_PENDING;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  QResult R;
+  std::memcpy(&R, (const void*)&sv->hres[idx], sizeof(R));
+  const unsigned slot = R.slot;
+  int rc = (int)R.status;
+  if (rc == OPMOS_OK) {
+    opmos_result* r = nullptr;
+    rc = take_result(R, sv->qd[idx], !(sv->o.flags & OPMOS_FLAG_NO_PATHS), sv->pool_words[slot], sv->hstream, &r);
+    if (rc == OPMOS_OK) {
+      fill_stats(&r->stats, R, sv->qd[idx]);
+      *out = r;
+    }
+  } else {
+    search_status((unsigned)rc);
+  }
+  // the result has been copied: the slot may take the next query
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  *reinterpret_cast<volatile unsigned*>(&sv->hctl[HC_RELEASE + slot]) = 1;
+  sv->hdone[idx] = 0;
+  sv->inuse[idx] = 0;
+  return rc;
+}
+
+void opmos_server_destroy(opmos_server* sv) {
+  if (!sv) return;
+  server_free(sv);
+}
 
 }  // extern "C"

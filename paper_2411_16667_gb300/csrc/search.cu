@@ -1117,9 +1117,12 @@ __device__ bool mq_barrier(MCtl* M) {
 }
 
 // P0: slot transitions and admission (block 0).
-__device__ void mq_write_result(const MSlot& sl, QCtl* C, QResult* results) {
-  QResult* R = &results[sl.qidx];
+__device__ void mq_write_result(const MSlot& sl, unsigned slot, QCtl* C, QResult* results, unsigned* done_flags,
+                                unsigned qcap) {
+  const unsigned ri = sl.qidx % qcap;
+  QResult* R = &results[ri];
   R->status = ld_volatile(&C->error);
+  R->slot = slot;
   R->count = C->res_count;
   R->off = C->res_off;
   R->path = C->res_path;
@@ -1129,9 +1132,15 @@ __device__ void mq_write_result(const MSlot& sl, QCtl* C, QResult* results) {
   C->stats[S_STEPS] = C->step;
   C->stats[S_GOALINS] = C->plog_len;
   for (int i = 0; i < kNStat; ++i) R->stats[i] = C->stats[i];
+  if (done_flags) {
+    __threadfence_system();  // the record is visible before its completion flag
+    *reinterpret_cast<volatile unsigned*>(&done_flags[ri]) = 1u;
+    __threadfence_system();
+  }
 }
 
-__device__ void mq_alloc_region1(const MSlot& sl, QCtl* C, const OutPool& O) {
+__device__ void mq_alloc_region1(const MSlot& sl, QCtl* C) {
+  const OutPool& O = sl.O;
   const unsigned kk_live = ld_volatile(&C->res_count);
   const unsigned long long words = (unsigned long long)kk_live * sl.d + kk_live + 1;
   const unsigned long long off = atomicAdd(O.used, words);
@@ -1139,13 +1148,14 @@ __device__ void mq_alloc_region1(const MSlot& sl, QCtl* C, const OutPool& O) {
   C->res_off = off;
 }
 
-__device__ void mq_schedule(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue,
-                            const unsigned* q_count_ptr, const GraphDev* graphs, MCtl* M, QResult* results,
-                            const OutPool& O) {
+__device__ void mq_schedule(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue, unsigned* hctl,
+                            const GraphDev* graphs, MCtl* M, QResult* results, unsigned* done_flags) {
   __shared__ unsigned s_busy;
   if (threadIdx.x == 0) s_busy = 0;
   __syncthreads();
-  const unsigned q_count = ld_volatile(q_count_ptr);
+  const unsigned q_count = ld_volatile(&hctl[HC_TAIL]);
+  const unsigned qcap = M->qcap;
+  const unsigned after_out = M->hold ? SL_HELD : SL_FREE;
   for (unsigned q = threadIdx.x; q < nslots; q += blockDim.x) {
     MSlot& sl = slots[q];
     QCtl* C = &ctls[q];
@@ -1166,19 +1176,22 @@ __device__ void mq_schedule(MSlot* slots, QCtl* ctls, unsigned nslots, const MQu
     } else if (st == SL_OUT1 || st == SL_OUT2 || st == SL_OUT3 || st == SL_OUT4) {
       // one output part per iteration; an error ends the output early
       if (ld_volatile(&C->error) || st == SL_OUT4) {
-        mq_write_result(sl, C, results);
-        st = SL_FREE;
+        mq_write_result(sl, q, C, results, done_flags, qcap);
+        st = after_out;
       } else if (st == SL_OUT1) {
-        mq_alloc_region1(sl, C, O);
+        mq_alloc_region1(sl, C);
         if (ld_volatile(&C->error)) {  // no room for the result: report, never write
-          mq_write_result(sl, C, results);
-          st = SL_FREE;
+          mq_write_result(sl, q, C, results, done_flags, qcap);
+          st = after_out;
         } else {
           st = SL_OUT2;
         }
       } else {
         st = st + 1;
       }
+    } else if (st == SL_HELD && ld_volatile(&hctl[HC_RELEASE + q])) {
+      hctl[HC_RELEASE + q] = 0;  // the host has collected the result
+      st = SL_FREE;
     }
     if (st == SL_FREE) {
       unsigned qn = ld_volatile(&M->q_next);
@@ -1188,13 +1201,22 @@ __device__ void mq_schedule(MSlot* slots, QCtl* ctls, unsigned nslots, const MQu
         qn = got;
       }
       if (qn < q_count) {
-        const MQuery Q = queue[qn];
+        MQuery Q;
+        {
+          const volatile MQuery* src = &queue[qn % qcap];
+          Q.graph = src->graph;
+          Q.start = src->start;
+          Q.goal = src->goal;
+          Q.d = src->d;
+          Q.h = src->h;
+        }
         sl.P.start = Q.start;
         sl.P.goal = Q.goal;
         sl.P.h = Q.h;
         sl.G = graphs[Q.graph];
         sl.d = Q.d;
         sl.qidx = qn;
+        if (M->hold) *sl.O.used = 0;  // serving: the slot's own pool starts empty (batch pools are shared)
         st = SL_INIT;
       }
     }
@@ -1204,17 +1226,18 @@ __device__ void mq_schedule(MSlot* slots, QCtl* ctls, unsigned nslots, const MQu
   __syncthreads();
   if (threadIdx.x == 0) {
     M->iter++;
-    if (s_busy == 0 && ld_volatile(&M->q_next) >= ld_volatile(q_count_ptr) && ld_volatile(&M->closing))
-      M->done = 1;
+    const unsigned closing = ld_volatile(&hctl[HC_CLOSING]);
+    if (closing >= 2 || (closing && s_busy == 0 && ld_volatile(&M->q_next) >= ld_volatile(&hctl[HC_TAIL])))
+      M->done = 1;  // 1: drain then stop; 2: stop now
   }
 }
 
 template <int D>
-__device__ void mq_work(MSlot* slots, QCtl* ctls, unsigned q, unsigned j, unsigned nb, unsigned ph,
-                        const OutPool& O, QResult* results, Shared& S) {
+__device__ void mq_work(MSlot* slots, QCtl* ctls, unsigned q, unsigned j, unsigned nb, unsigned ph, Shared& S) {
   const QArena A = slots[q].A;
   const QParams P = slots[q].P;
   const GraphDev G = slots[q].G;
+  const OutPool O = slots[q].O;
   const unsigned st = slots[q].state;
   QCtl* C = &ctls[q];
   Search<D> X(G, A, C, P, O, S);
@@ -1275,8 +1298,7 @@ __device__ __forceinline__ unsigned mq_weight(const MSlot& sl, QCtl* C, unsigned
   return w ? w : 1u;  // a running slot always gets a block (index builds run in every phase)
 }
 
-__device__ void mq_phase(unsigned ph, MSlot* slots, QCtl* ctls, unsigned nslots, const OutPool& O,
-                         QResult* results, Shared& S, unsigned* s_pref) {
+__device__ void mq_phase(unsigned ph, MSlot* slots, QCtl* ctls, unsigned nslots, Shared& S, unsigned* s_pref) {
   // total weight of the multi-block slots
   __shared__ unsigned long long s_wtot;
   if (threadIdx.x == 0) s_wtot = 0;
@@ -1323,7 +1345,7 @@ __device__ void mq_phase(unsigned ph, MSlot* slots, QCtl* ctls, unsigned nslots,
     switch (slots[q].d) {
 #define MQ_CASE(DD) \
   case DD:          \
-    mq_work<DD>(slots, ctls, q, j, nb, ph, O, results, S); \
+    mq_work<DD>(slots, ctls, q, j, nb, ph, S); \
     break;
       MQ_CASE(1) MQ_CASE(2) MQ_CASE(3) MQ_CASE(4) MQ_CASE(5) MQ_CASE(6) MQ_CASE(7) MQ_CASE(8)
 #undef MQ_CASE
@@ -1335,16 +1357,16 @@ __device__ void mq_phase(unsigned ph, MSlot* slots, QCtl* ctls, unsigned nslots,
 }
 
 __global__ void __launch_bounds__(kMultiThreads, 2)
-    multi_kernel(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue, const unsigned* q_count_ptr,
-                 const GraphDev* graphs, OutPool O, QResult* results, MCtl* M) {
+    multi_kernel(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue, unsigned* hctl,
+                 const GraphDev* graphs, QResult* results, unsigned* done_flags, MCtl* M) {
   __shared__ Shared S;
   __shared__ unsigned s_pref[kMaxSlots + 1];
   for (;;) {
-    if (blockIdx.x == 0) mq_schedule(slots, ctls, nslots, queue, q_count_ptr, graphs, M, results, O);
+    if (blockIdx.x == 0) mq_schedule(slots, ctls, nslots, queue, hctl, graphs, M, results, done_flags);
     if (!mq_barrier(M)) return;
     if (ld_volatile(&M->done)) return;
     for (unsigned ph = 1; ph <= 3; ++ph) {
-      mq_phase(ph, slots, ctls, nslots, O, results, S, s_pref);
+      mq_phase(ph, slots, ctls, nslots, S, s_pref);
       if (!mq_barrier(M)) return;
     }
   }
@@ -1388,11 +1410,11 @@ cudaError_t launch_search_grid(unsigned d, const GraphDev& G, const QArena& A, Q
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_multi(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue,
-                         const unsigned* q_count_ptr, const GraphDev* graphs, const OutPool& O, QResult* results,
-                         MCtl* M, unsigned blocks, cudaStream_t s) {
-  void* args[] = {(void*)&slots, (void*)&ctls, (void*)&nslots, (void*)&queue, (void*)&q_count_ptr,
-                  (void*)&graphs, (void*)&O, (void*)&results, (void*)&M};
+cudaError_t launch_multi(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue, unsigned* hctl,
+                         const GraphDev* graphs, QResult* results, unsigned* done_flags, MCtl* M,
+                         unsigned blocks, cudaStream_t s) {
+  void* args[] = {(void*)&slots, (void*)&ctls, (void*)&nslots, (void*)&queue, (void*)&hctl,
+                  (void*)&graphs, (void*)&results, (void*)&done_flags, (void*)&M};
   return cudaLaunchCooperativeKernel((void*)multi_kernel, dim3(blocks), dim3(kMultiThreads), args, 0, s);
 }
 

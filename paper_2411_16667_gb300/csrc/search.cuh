@@ -8,12 +8,16 @@ namespace opmos {
 // Multi-query kernel (batch and serving) --------------------------------------
 constexpr unsigned kMultiThreads = 256;  // threads per block
 constexpr unsigned kMaxSlots = 1024;     // concurrent queries
-enum SlotState : unsigned { SL_FREE = 0, SL_INIT = 1, SL_RUN = 2, SL_OUT1 = 3, SL_OUT2 = 4, SL_OUT3 = 5, SL_OUT4 = 6 };
+enum SlotState : unsigned {
+  SL_FREE = 0, SL_INIT = 1, SL_RUN = 2, SL_OUT1 = 3, SL_OUT2 = 4, SL_OUT3 = 5, SL_OUT4 = 6,
+  SL_HELD = 7  // result written, waiting for the host to collect it (serving)
+};
 
 struct MSlot {     // one concurrent query: its arena and current parameters
   QArena A;
   QParams P;
   GraphDev G;
+  OutPool O;       // where its result goes (shared in batch mode, its own when serving)
   unsigned d, state, qidx, pad;
 };
 
@@ -24,15 +28,21 @@ struct MQuery {    // a queued query
 
 struct MCtl {      // grid-wide control of the multi-query kernel
   unsigned bar_count, bar_gen, error, done;
-  unsigned q_next, closing, iter, pad;
+  unsigned q_next, iter, qcap, hold;  // hold: keep slots until the host releases them
 };
+
+// Host control words (host-mapped memory when serving): [0] queries queued
+// so far, [1] closing (no more queries will come), [2 + slot] release flag.
+enum { HC_TAIL = 0, HC_CLOSING = 1, HC_RELEASE = 2 };
 
 // Result descriptor of one query, written by the team leader at the end.
 // Output words (in the OutPool): at off, count*d costs (lexicographic) then
 // count+1 path offsets; at path, total node ids then total-count arc ids.
 struct QResult {
   unsigned status;
+  unsigned slot;    // slot whose output pool holds the result
   unsigned count;
+  unsigned pad;
   unsigned long long off;
   unsigned long long path;
   unsigned long long total;
@@ -44,9 +54,9 @@ struct QResult {
 cudaError_t launch_search_grid(unsigned d, const GraphDev& G, const QArena& A, QCtl* C, const QParams& P,
                                const OutPool& O, QResult* R, unsigned blocks, cudaStream_t s);
 int search_occupancy(unsigned d, int batch);
-cudaError_t launch_multi(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue,
-                         const unsigned* q_count_ptr, const GraphDev* graphs, const OutPool& O, QResult* results,
-                         MCtl* M, unsigned blocks, cudaStream_t s);
+cudaError_t launch_multi(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue, unsigned* hctl,
+                         const GraphDev* graphs, QResult* results, unsigned* done_flags, MCtl* M,
+                         unsigned blocks, cudaStream_t s);
 int multi_occupancy();
 
 // Ideal-point heuristic jobs: h_out[v] = shortest v->goal distance under

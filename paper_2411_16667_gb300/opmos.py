@@ -247,3 +247,44 @@ def opmos_solve_batch(graph: opmos_graph, starts, goals, options: Options | None
         r = outs[q]
         results.append((int(status[q]), _take(ctypes.c_void_p(r)) if r else None))
     return results
+
+
+class opmos_server:
+    """Continuous-batching server (opmos_server_create/submit/poll/destroy)."""
+
+    def __init__(self, graphs, options: Options | None = None, **kw):
+        self.graphs = list(graphs)
+        arr = (ctypes.c_void_p * len(self.graphs))(*[g.handle.value for g in self.graphs])
+        o = options or _options(**kw)
+        h = ctypes.c_void_p()
+        _check(lib().opmos_server_create(ctypes.cast(arr, ctypes.c_void_p), len(self.graphs), ctypes.byref(o),
+                                         ctypes.byref(h)), "opmos_server_create")
+        self.handle = h
+
+    def submit(self, graph: int, d: int, start: int, goal: int) -> int:
+        t = ctypes.c_uint64()
+        _check(lib().opmos_server_submit(self.handle, graph, d, start, goal, ctypes.byref(t)), "opmos_server_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """(PENDING, None) until done; then (status, Result or None)."""
+        res = ctypes.c_void_p()
+        rc = lib().opmos_server_poll(self.handle, ticket, ctypes.byref(res))
+        if rc == PENDING:
+            return PENDING, None
+        if rc == OK:
+            return OK, _take(res)
+        if rc == ERR_INVALID_ARG and not res.value:
+            _check(rc, "opmos_server_poll")
+        return rc, None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().opmos_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
