@@ -175,7 +175,7 @@ int plan_arena(const opmos_graph* g, uint32_t D, uint32_t window, size_t budget,
   pl->cand_cap = pl->win_cap * std::max<uint32_t>(g->maxdeg, 1);
   pl->plog_cap = batch ? (1u << 16) : (1u << 20);
   const size_t ptiles = pl->plog_cap / 32 + 1;
-  size_t fixed = n * (8 + 4 + 4 + 4) + 2 * kNB * 4 + (size_t)pl->win_cap * 4 +
+  size_t fixed = (n + 1) * (8 + 4 + 4 + 4) + 2 * kNB * 4 + (size_t)pl->win_cap * 4 +
                  (size_t)pl->cand_cap * (16 + 4 * D + 4) + (size_t)pl->plog_cap * 4 * D +
                  2 * ((size_t)pl->plog_cap + ptiles) * 4 * D + 64 * 256;
   if (budget < fixed + (8u << 20))
@@ -194,7 +194,7 @@ int plan_arena(const opmos_graph* g, uint32_t D, uint32_t window, size_t budget,
 
 void layout_arena(const opmos_graph* g, uint32_t D, const ArenaPlan& pl, char* base, QArena* A) {
   char* p = base;
-  const size_t n = g->n;
+  const size_t n = g->n + 1;  // the last node stands for P (extracted goal labels)
   A->fbase = carve<uint64_t>(p, n);
   A->fcount = carve<uint32_t>(p, n);
   A->fcap = carve<uint32_t>(p, n);

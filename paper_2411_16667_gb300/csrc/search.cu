@@ -20,8 +20,10 @@
 //                  (Alg. 1 l.22-28: weakly dominated candidates are dropped,
 //                  strictly dominated frontier labels are pruned), then against
 //                  P on F (Alg. 1 l.29); survivors become labels, join alpha(v')
-//                  and OPEN. At the goal node alpha(v_g) is P itself (Alg. 1
-//                  l.11-13) and survivors are appended to the P log.
+//                  and OPEN. Goal labels are ordinary labels until they are
+//                  extracted (Alg. 1 l.6-8); an extracted goal label is sent
+//                  to a virtual node n that stands for P, whose merge applies
+//                  Alg. 1 l.11-13 and appends survivors to the P log.
 //
 // The F-against-P test of phase 4 uses an index of P rebuilt every time P has
 // grown by about 1/8: P sorted along a Z-order curve over objectives 1..3 in
@@ -160,7 +162,7 @@ struct Search {
   // barrier before init_seed writes the start node's frontier.
   template <class Team>
   __device__ void init_zero(const Team& T) {
-    for (unsigned v = T.tid(); v < G.n; v += T.nthreads()) {
+    for (unsigned v = T.tid(); v <= G.n; v += T.nthreads()) {  // n real nodes + P
       A.fcount[v] = 0;
       A.fcap[v] = 0;
       A.fbase[v] = 0;
@@ -194,9 +196,10 @@ struct Search {
       A.ledge[0] = kInf;
       A.lpver[0] = 0;
       A.lstatus[0] = (s == t) ? ST_CLOSED : ST_OPEN;
-      A.fbase[s] = 0;
-      A.fcap[s] = tile;
-      A.fcount[s] = 1;
+      const uint32_t fs = (s == t) ? G.n : s;  // start == goal: l_s is the solution
+      A.fbase[fs] = 0;
+      A.fcap[fs] = tile;
+      A.fcount[fs] = 1;
 #pragma unroll
       for (int k = 0; k < D; ++k) A.fpool[(size_t)k * tile] = 0;
       A.fpool[(size_t)D * tile] = 0;
@@ -422,6 +425,22 @@ struct Search {
     uint32_t g[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) g[k] = A.lg[(size_t)k * A.label_cap + id];
+    if (v == P.goal) {
+      // Alg. 1 l.8: a goal label is not expanded; it goes to P (virtual node n)
+      if (gl == 0) {
+        const uint32_t vp = G.n;
+        const unsigned c = agg_inc(&C->cand_count);
+        A.cnode[c] = vp;
+        A.cparent[c] = A.lparent[id];
+        A.cedge[c] = A.ledge[id];
+#pragma unroll
+        for (int k = 0; k < D; ++k) A.cg[(size_t)k * A.cand_cap + c] = g[k];
+        const int old = atomicExch(&A.node_head[vp], (int)c);
+        A.cnext[c] = old;
+        if (old == kNil) A.touched[agg_inc(&C->touched_count)] = vp;
+      }
+      return;
+    }
     const uint32_t e0 = __ldg(G.rowptr + v), e1 = __ldg(G.rowptr + v + 1);
     for (uint32_t e = e0 + gl; e < e1; e += L) {
       const uint32_t v2 = __ldg(G.col + e);
@@ -615,7 +634,7 @@ struct Search {
                               unsigned pcount, unsigned pntiles, unsigned pbuf) {
     const unsigned lane = lane_id();
     const unsigned nxt = cur ^ 1u;
-    const bool is_goal = (v == P.goal);
+    const bool is_goal = (v == G.n);  // the virtual node standing for P
     uint32_t c[D];
     const bool valid = lane < nb;
 #pragma unroll
@@ -759,7 +778,7 @@ struct Search {
           const unsigned id = lb + r;
 #pragma unroll
           for (int k = 0; k < D; ++k) A.lg[(size_t)k * A.label_cap + id] = c[k];
-          A.lnode[id] = v;
+          A.lnode[id] = is_goal ? P.goal : v;
           A.lparent[id] = A.cparent[mine];
           A.ledge[id] = A.cedge[mine];
           A.lpver[id] = psnap;
@@ -842,7 +861,7 @@ struct Search {
   // dominates; C->res_count must be 0 beforehand.
   template <class Team>
   __device__ void out_filter(const Team& T) {
-    const uint32_t t = P.goal;
+    const uint32_t t = G.n;  // P
     const unsigned k = A.fcount[t];
     const uint64_t fb = A.fbase[t];
     const unsigned cap = A.fcap[t];
@@ -882,7 +901,7 @@ struct Search {
   // (2b) lexicographic rank of every kept member; costs and path lengths.
   template <class Team>
   __device__ void out_rank(const Team& T) {
-    const uint32_t t = P.goal;
+    const uint32_t t = G.n;  // P
     const unsigned k = A.fcount[t];
     const uint64_t fb = A.fbase[t];
     const unsigned cap = A.fcap[t];
@@ -950,7 +969,7 @@ struct Search {
   template <class Team>
   __device__ void out_paths(const Team& T) {
     if (P.flags & OPMOS_FLAG_NO_PATHS) return;
-    const uint32_t t = P.goal;
+    const uint32_t t = G.n;  // P
     const unsigned k = A.fcount[t];
     const uint64_t fb = A.fbase[t];
     const unsigned cap = A.fcap[t];
@@ -1280,7 +1299,7 @@ __device__ void mq_work(MSlot* slots, QCtl* ctls, unsigned q, unsigned j, unsign
   }
 }
 
-__device__ __forceinline__ unsigned A_fcount_goal(const MSlot& sl) { return sl.A.fcount[sl.P.goal]; }
+__device__ __forceinline__ unsigned A_fcount_goal(const MSlot& sl) { return sl.A.fcount[sl.G.n]; }
 
 // Work units of a slot in phase ph (0: none). INIT and the scan part of the
 // output get one block; the other output parts a share like search phases.

@@ -81,8 +81,13 @@ def write_digests(args):
         g = g.first_objectives(args.d)
     jobs = [(args.config, args.seed, args.d, args.budget, qi) for qi in range(len(queries))]
     ctx = mp.get_context("spawn")
+    lines = [None] * len(jobs)
     with ctx.Pool(args.jobs) as pool:
-        lines = pool.map(_digest_job, jobs, chunksize=4)
+        for line in pool.imap_unordered(_digest_job, jobs):
+            lines[int(line.split()[0])] = line
+            done = sum(x is not None for x in lines)
+            if done % 64 == 0:
+                print(f"{done}/{len(jobs)} queries", flush=True)
     suffix = f"_d{args.d}" if args.d else ""
     path = os.path.join(HERE, f"{args.config}_seed{args.seed}{suffix}.digests")
     with open(path + ".tmp", "w") as f:
