@@ -18,7 +18,18 @@ e2e    = the same metric through the C ABI with host buffers: graph upload,
 --impl reference times the oracle (sequential NAMOA*, Algorithm 1) on the host
 cores on a bounded sample of the same query (a label budget).
 
+Other workloads (--workload):
+  ship128-d3        the same recipe on a 128x128 grid: the small case used for
+                    ncu captures (value = the GPU's own labels/s)
+  ship256-d5-batch  1,024 start/goal pairs (Chebyshev distance 16-128) on the
+                    5-objective ship grid in one continuous-batching launch;
+                    value = queries/s, beside one query per launch on a sample
+  serve             Poisson arrivals over the device-resident 32x32, 256x256 and
+                    200k-node graphs, d ~ U{2..5} clamped, at three rates;
+                    p50/p99 latency and queries/s beside one query per launch
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                       [--workload NAME]
 """
 from __future__ import annotations
 
@@ -152,6 +163,178 @@ def workload_config():
             "l2": "inputs and search state exceed L2; a 256 MiB buffer is also written between steps"}
 
 
+def _peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured hbm_gbs (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def run_small(args, opmos, torch, stream):
+    """128x128 ship grid, one query: the small case for profiler captures."""
+    g, q = synth.ship_grid(2, 128, 3)
+    s, t = q[0]
+    G = opmos.opmos_graph.from_synth(g)
+    opt = opmos.opmos_default_options(stream=stream.cuda_stream, window=args.window or None)
+    for _ in range(args.warmup):
+        opmos.opmos_solve(G, s, t, options=opt)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        r = opmos.opmos_solve(G, s, t, options=opt)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    st = r.stats
+    peak, src = _peak()
+    ach = st["bytes"] / (st["search_ns"] / 1e9) / 1e9
+    print(json.dumps({"metric": "labels/s (GPU extractions, small profiling case)", "value": st["extracted"] / (ms / 1e3),
+                      "unit": "labels/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+                      "config": {"workload": "ship128-d3: 128x128 ship grid, d=3, corner to corner, seed 2"},
+                      "front_size": int(r.costs.shape[0]), "search_kernel_ms": st["search_ns"] / 1e6,
+                      "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                   "frac": ach / peak, "peak_source": src}}), flush=True)
+
+
+def run_batch(args, opmos, torch, stream):
+    """Config 4: 1,024 queries in one continuous-batching launch."""
+    g, q = synth.config4(1)
+    G = opmos.opmos_graph.from_synth(g)
+    starts = [s for s, _ in q]
+    goals = [t for _, t in q]
+    opt = opmos.Options()
+    opt.stream = stream.cuda_stream
+    if args.window:
+        opt.window = args.window
+    for _ in range(args.warmup):
+        opmos.opmos_solve_batch(G, starts, goals, options=opt)
+    torch.cuda.synchronize()
+    times, stats = [], None
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            out = opmos.opmos_solve_batch(G, starts, goals, options=opt)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+    ok = sum(1 for st, _ in out if st == opmos.OK)
+    rs = [r for _, r in out if r is not None]
+    sec = statistics.median(times)
+    # one query per launch on an evenly spaced sample of the same queries
+    sample = q[::16]
+    single = opmos.opmos_default_options(stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    for s_, t_ in sample:
+        opmos.opmos_solve(G, s_, t_, options=single)
+    torch.cuda.synchronize()
+    single_qps = len(sample) / (time.perf_counter() - t0)
+    print(json.dumps({"metric": "batched queries/s", "value": len(q) / sec, "unit": "queries/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                      "data": "synthetic",
+                      "config": {"workload": "ship256-d5-batch: 1,024 queries, Chebyshev 16-128, 5 objectives, seed 1"},
+                      "queries_ok": ok, "labels_extracted": sum(r.stats["extracted"] for r in rs),
+                      "labels_per_s": sum(r.stats["extracted"] for r in rs) / sec,
+                      "batch_kernel_ms": statistics.median(r.stats["search_ns"] for r in rs) / 1e6,
+                      "heuristic_ms": rs[0].stats["heuristic_ns"] / 1e6,
+                      "one_query_per_launch_qps": single_qps,
+                      "one_query_per_launch_sample": f"{len(sample)} of the 1,024 queries (every 16th)",
+                      "batched_over_single": (len(q) / sec) / single_qps, "clocks": clk.summary()}), flush=True)
+
+
+def serve_queries(n, seed=5):
+    """Config-5 query stream over configs 1-3: graph uniform, d ~ U{2..5}
+    clamped to the graph's objective count, start/goal as in each config."""
+    g1, q1 = synth.config1()
+    g2, q2 = synth.config2()
+    g3, q3 = synth.config3()
+    graphs = [g1, g2, g3]
+    qsets = [q1, q2, q3]
+    out = []
+    for i in range(n):
+        gi = int(synth.rand_int(seed, 900, i, 0, 2))
+        d = min(int(synth.rand_int(seed, 901, i, 2, 5)), graphs[gi].d)
+        qs = qsets[gi]
+        s, t = qs[int(synth.rand_int(seed, 902, i, 0, len(qs) - 1))]
+        out.append((gi, d, s, t))
+    return graphs, out
+
+
+def run_serve(args, opmos, torch, stream):
+    """Config 5: continuous-batching server under Poisson arrivals."""
+    import random
+    budget = args.serve_label_budget
+    graphs, plan = serve_queries(args.serve_queries * 5)
+    G = [opmos.opmos_graph.from_synth(g) for g in graphs]
+    # one query per launch on the first queries of the stream (no server resident)
+    single = opmos.opmos_default_options(stream=stream.cuda_stream, label_budget=budget)
+    t0 = time.perf_counter()
+    n_single = args.serve_queries
+    single_status = []
+    for gi, d, s, t in plan[:n_single]:
+        single.d_used = d
+        try:
+            opmos.opmos_solve(G[gi], s, t, options=single)
+            single_status.append(0)
+        except opmos.OpmosError as e:
+            single_status.append(e.code)
+    torch.cuda.synchronize()
+    single_qps = n_single / (time.perf_counter() - t0)
+    srv = opmos.opmos_server(G, label_budget=budget, window=args.window or 256)
+
+    def run(queries, rate):
+        """Submit with Poisson arrivals at `rate` q/s (0: all at once)."""
+        rnd = random.Random(7)
+        pending, lat, status = {}, [], []
+        t_next = time.perf_counter()
+        i = 0
+        t_start = time.perf_counter()
+        while i < len(queries) or pending:
+            now = time.perf_counter()
+            while i < len(queries) and now >= t_next:
+                try:
+                    tk = srv.submit(*queries[i])
+                    pending[tk] = time.perf_counter()
+                    i += 1
+                    t_next += rnd.expovariate(rate) if rate > 0 else 0.0
+                except opmos.OpmosError:
+                    break  # queue full: retry on the next pass
+                now = time.perf_counter()
+            for tk in list(pending):
+                st, _ = srv.poll(tk)
+                if st != opmos.PENDING:
+                    lat.append(time.perf_counter() - pending.pop(tk))
+                    status.append(st)
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t_start
+        lat.sort()
+        return {"queries": len(queries), "qps": len(queries) / wall,
+                "p50_ms": 1e3 * lat[len(lat) // 2], "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                "ok": sum(1 for x in status if x == opmos.OK),
+                "budget_exceeded": sum(1 for x in status if x == opmos.ERR_BUDGET),
+                "capacity": sum(1 for x in status if x == opmos.ERR_CAPACITY)}
+
+    n = args.serve_queries
+    sat = run(plan[n:2 * n], 0.0)
+    rates = {}
+    with ClockSampler(0) as clk:
+        for k, frac in enumerate((0.25, 0.5, 0.9)):
+            r = frac * sat["qps"]
+            rates[f"{frac:.2f}x"] = {"rate_qps": r, **run(plan[(2 + k) * n:(3 + k) * n], r)}
+    srv.close()
+    best = max(v["qps"] for v in rates.values())
+    print(json.dumps({"metric": "served queries/s and p50/p99 latency", "value": sat["qps"], "unit": "queries/s",
+                      "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+                      "config": {"workload": "serve: configs 1-3 graphs resident, d ~ U{2..5} clamped, Poisson arrivals",
+                                 "label_budget_per_query": budget, "queries_per_rate": n},
+                      "saturation": sat, "rates": rates, "one_query_per_launch_qps": single_qps,
+                      "one_query_per_launch_ok": sum(1 for x in single_status if x == 0),
+                      "served_over_single": sat["qps"] / single_qps, "best_rate_qps": best,
+                      "clocks": clk.summary()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -161,6 +344,10 @@ def main():
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--cpu-labels", type=int, default=CPU_SAMPLE_LABELS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-queries", type=int, default=48)
+    ap.add_argument("--serve-label-budget", type=int, default=2_000_000)
+    ap.add_argument("--workload", default="ship256-d3",
+                    choices=["ship256-d3", "ship128-d3", "ship256-d5-batch", "serve"])
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -172,6 +359,14 @@ def main():
     from paper_2411_16667_gb300 import opmos
 
     torch.cuda.set_device(local)
+    if args.workload != "ship256-d3":
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            if args.workload == "ship128-d3":
+                return run_small(args, opmos, torch, stream)
+            if args.workload == "ship256-d5-batch":
+                return run_batch(args, opmos, torch, stream)
+            return run_serve(args, opmos, torch, stream)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))

@@ -80,7 +80,7 @@ typedef struct opmos_options {
   uint64_t label_budget;     /* max labels a query may create; exceeding it is
                                 OPMOS_ERR_BUDGET. Default: unlimited (arena-bound). */
   uint64_t mem_budget_bytes; /* device arena per query (single) or per batch (batch).
-                                Default: 8 GiB single, 96 GiB batch. */
+                                Default: 8 GiB single, 160 GiB batch. */
   uint32_t d_used;           /* use only the first d_used objectives (Table 1 order rule,
                                 Sec. 6.1). Default: all. */
   uint32_t flags;            /* OPMOS_FLAG_* */

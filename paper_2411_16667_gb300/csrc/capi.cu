@@ -136,7 +136,7 @@ opmos_options resolve(const opmos_options* in, bool batch) {
   opmos_default_options(&o);
   if (batch) {
     o.window = 256;
-    o.mem_budget_bytes = 96ull << 30;
+    o.mem_budget_bytes = 160ull << 30;
   }
   if (!in) return o;
   if (in->window) o.window = in->window;
