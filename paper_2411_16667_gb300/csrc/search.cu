@@ -26,7 +26,7 @@
 //                  Alg. 1 l.11-13 and appends survivors to the P log.
 //
 // The F-against-P test of phase 4 uses an index of P rebuilt every time P has
-// grown by about 1/8: P sorted along a Z-order curve over objectives 1..3 in
+// grown by about 1/16: P sorted along a Z-order curve over objectives 1..3 in
 // tiles of 32, each with its componentwise minimum; a candidate only scans the
 // tiles whose minimum weakly dominates it, plus the goal costs found since the
 // last rebuild (the rebuild is split over phases 1-3 of a step).
@@ -288,7 +288,7 @@ struct Search {
     __syncthreads();
     if (D < 2) return;
     const unsigned plen = ld_volatile(&C->plog_len);
-    const bool build = plen - C->ps_mark > 32u + C->ps_count / 8u && plen <= kPSMax;
+    const bool build = plen - C->ps_mark > 32u + C->ps_count / 16u && plen <= kPSMax;
     if (threadIdx.x == 0) S.pmax[0] = S.pmax[1] = S.pmax[2] = 0;
     __syncthreads();
     if (!build) return;
@@ -377,12 +377,12 @@ struct Search {
   // is never taken). Every block computes the same b*.
   __device__ unsigned select_bucket(unsigned cur) {
     const unsigned* gh = A.hist + cur * kNB;
-    const unsigned per = kNB / blockDim.x;  // blockDim divides kNB
+    const unsigned per = (kNB + blockDim.x - 1) / blockDim.x;  // blockDim >= 64
     const unsigned b0 = threadIdx.x * per;
     unsigned loc[kNB / 64 > 0 ? kNB / 64 : 1];
     unsigned sum = 0;
     for (unsigned j = 0; j < per; ++j) {
-      loc[j] = *reinterpret_cast<const volatile unsigned*>(&gh[b0 + j]);
+      loc[j] = b0 + j < (unsigned)kNB ? *reinterpret_cast<const volatile unsigned*>(&gh[b0 + j]) : 0u;
       sum += loc[j];
     }
     if (threadIdx.x == 0) {
@@ -564,23 +564,32 @@ struct Search {
   __device__ void p_filter(bool& alive, const uint32_t (&F)[D], unsigned t0, unsigned t1, unsigned pcount,
                            unsigned pntiles, unsigned pbuf, unsigned long long& pcmp) {
     const unsigned lane = lane_id();
-    for (unsigned j0 = t0; j0 < t1; j0 += 32) {
-      unsigned amask = __ballot_sync(0xffffffffu, alive);
-      if (!amask) return;
-      const unsigned jj = j0 + lane;
-      const bool vp = jj < t1;
-      uint32_t p[D];
+    constexpr int UT = 4;  // tail tiles loaded per round
+    for (unsigned r0 = t0; r0 < t1; r0 += 32 * UT) {
+      if (!__any_sync(0xffffffffu, alive)) return;
+      uint32_t pt[UT][D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) p[k] = vp ? A.plog[(size_t)k * A.plog_cap + jj] : kInf;
-      pcmp += (unsigned long long)__popc(amask) * min(32u, t1 - j0);
-      while (amask) {
-        const unsigned j = __ffs(amask) - 1;
-        amask &= amask - 1;
-        uint32_t Fj[D];
+      for (int u = 0; u < UT; ++u) {
+        const unsigned jj = r0 + u * 32 + lane;
 #pragma unroll
-        for (int k = 0; k < D; ++k) Fj[k] = __shfl_sync(0xffffffffu, F[k], j);
-        const bool wd = vp && weakly_le<D>(p, Fj);
-        if (__ballot_sync(0xffffffffu, wd) && lane == j) alive = false;
+        for (int k = 0; k < D; ++k) pt[u][k] = jj < t1 ? A.plog[(size_t)k * A.plog_cap + jj] : kInf;
+      }
+#pragma unroll
+      for (int u = 0; u < UT; ++u) {
+        const unsigned j0 = r0 + u * 32;
+        unsigned amask = __ballot_sync(0xffffffffu, alive);
+        if (j0 >= t1 || !amask) break;
+        const bool vp = j0 + lane < t1;
+        pcmp += (unsigned long long)__popc(amask) * min(32u, t1 - j0);
+        while (amask) {
+          const unsigned j = __ffs(amask) - 1;
+          amask &= amask - 1;
+          uint32_t Fj[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) Fj[k] = __shfl_sync(0xffffffffu, F[k], j);
+          const bool wd = vp && weakly_le<D>(pt[u], Fj);
+          if (__ballot_sync(0xffffffffu, wd) && lane == j) alive = false;
+        }
       }
     }
     if (!pcount) return;

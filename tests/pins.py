@@ -174,3 +174,19 @@ def load_front_fixture(path: str):
                 rows.append([int(x) for x in line.split()])
     costs = np.array(rows, dtype=np.uint32).reshape(-1, meta.get("d", 1))
     return meta, costs
+
+
+def check_front_sampled(g, s: int, t: int, costs: np.ndarray, paths, nrows: int = 1000, npaths: int = 100,
+                        seed: int = 0) -> None:
+    """The check_front contract for large fronts: cost-uniqueness on every
+    row, non-dominance for a sample of rows against every row (vectorised),
+    and path validity for a sample of paths."""
+    c = np.asarray(costs, dtype=np.int64)
+    assert np.unique(c, axis=0).shape[0] == c.shape[0], "front is not cost-unique"
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(c.shape[0], size=min(nrows, c.shape[0]), replace=False)
+    for r in rows:
+        le = np.all(c <= c[r], axis=1) & np.any(c < c[r], axis=1)
+        assert not le.any(), f"row {r} is dominated"
+    sel = rng.choice(len(paths), size=min(npaths, len(paths)), replace=False)
+    check_front(g, s, t, c[sel], [paths[i] for i in sel])
