@@ -88,6 +88,9 @@ typedef struct opmos_options {
 } opmos_options;
 
 #define OPMOS_FLAG_NO_PATHS 1u     /* skip path reconstruction (costs only) */
+#define OPMOS_FLAG_GRAPH 2u        /* batch: capture each launch (input uploads from pinned staging,
+                                      the persistent kernel, result downloads) into a CUDA graph and
+                                      replay it; a capture failure is reported as OPMOS_ERR_CUDA */
 
 /* Counters of one solve (sums over a batch for batch results). Sec. 6.2 lists
  * the paper's counters: extractions, candidate labels, solutions. */

@@ -91,6 +91,28 @@ struct Workspace {
 
 Workspace g_arena, g_out, g_scratch, g_misc;
 
+// A grow-only pinned host buffer (staging for captured launches).
+struct PinnedWorkspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int get(size_t want, void** out) {
+    if (want > bytes) {
+      if (ptr) cudaFreeHost(ptr);
+      ptr = nullptr;
+      bytes = 0;
+      cudaError_t e = cudaHostAlloc(&ptr, want, cudaHostAllocDefault);
+      if (e != cudaSuccess) {
+        ptr = nullptr;
+        return cuda_fail(e, "cudaHostAlloc(staging)");
+      }
+      bytes = want;
+    }
+    *out = ptr;
+    return OPMOS_OK;
+  }
+};
+PinnedWorkspace g_pinned;
+
 template <class T>
 T* carve(char*& p, size_t count, size_t align = 256) {
   uintptr_t a = reinterpret_cast<uintptr_t>(p);
@@ -542,33 +564,101 @@ int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const st
   std::vector<unsigned> hc(HC_RELEASE + slots, 0);
   hc[HC_TAIL] = nq;     // every query is queued up front
   hc[HC_CLOSING] = 1;   // and no more will come
-  CK(cudaMemsetAsync(used, 0, 8, s));
-  CK(cudaMemcpyAsync(hctl, hc.data(), hc.size() * 4, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(M, &hM, sizeof(MCtl), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(dgraphs, &g->dev, sizeof(GraphDev), cudaMemcpyHostToDevice, s));
-  CK(cudaMemsetAsync(ctls, 0, slots * sizeof(QCtl), s));
-  CK(cudaMemsetAsync(dres, 0, nq * sizeof(QResult), s));
-  CK(cudaMemcpyAsync(dslots, hslots.data(), slots * sizeof(MSlot), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(dqs, qs.data(), nq * sizeof(MQuery), cudaMemcpyHostToDevice, s));
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, s);
-  cudaError_t e = launch_multi(dslots, ctls, slots, dqs, hctl, dgraphs, dres, nullptr, M, blocks, s);
-  cudaEventRecord(e1, s);
   std::vector<QResult> hres(nq);
   MCtl hM2{};
-  cudaError_t e2 =
-      e == cudaSuccess ? cudaMemcpyAsync(hres.data(), dres, nq * sizeof(QResult), cudaMemcpyDeviceToHost, s) : e;
-  if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(&hM2, M, sizeof(MCtl), cudaMemcpyDeviceToHost, s);
-  cudaError_t e3 = cudaStreamSynchronize(s);
   float ms = 0;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (e != cudaSuccess) return cuda_fail(e, "multi-query launch");
-  if (e2 != cudaSuccess) return cuda_fail(e2, "batch status copy");
-  if (e3 != cudaSuccess) return cuda_fail(e3, "multi-query kernel");
+  if (o.flags & OPMOS_FLAG_GRAPH) {
+    // stage the inputs in pinned memory, capture uploads + kernel + downloads
+    const size_t b_hc = hc.size() * 4, b_sl = slots * sizeof(MSlot), b_q = nq * sizeof(MQuery),
+                 b_r = nq * sizeof(QResult);
+    void* pin = nullptr;
+    if (int rc = g_pinned.get(b_hc + sizeof(MCtl) * 2 + sizeof(GraphDev) + b_sl + b_q + b_r + 8 * 256, &pin))
+      return rc;
+    char* pp = (char*)pin;
+    unsigned* p_hc = carve<unsigned>(pp, hc.size());
+    MCtl* p_M = carve<MCtl>(pp, 1);
+    MCtl* p_M2 = carve<MCtl>(pp, 1);
+    GraphDev* p_g = carve<GraphDev>(pp, 1);
+    MSlot* p_sl = carve<MSlot>(pp, slots);
+    MQuery* p_q = carve<MQuery>(pp, nq);
+    QResult* p_r = carve<QResult>(pp, nq);
+    std::memcpy(p_hc, hc.data(), b_hc);
+    *p_M = hM;
+    *p_g = g->dev;
+    std::memcpy(p_sl, hslots.data(), b_sl);
+    std::memcpy(p_q, qs.data(), b_q);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // the legacy default stream cannot be captured: use a stream of our own
+    static cudaStream_t own = nullptr;
+    if (!s) {
+      if (!own) CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+      CK(cudaDeviceSynchronize());  // earlier default-stream work is complete
+      s = own;
+    }
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaMemsetAsync(used, 0, 8, s);
+      cudaMemcpyAsync(hctl, p_hc, b_hc, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(M, p_M, sizeof(MCtl), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(dgraphs, p_g, sizeof(GraphDev), cudaMemcpyHostToDevice, s);
+      cudaMemsetAsync(ctls, 0, slots * sizeof(QCtl), s);
+      cudaMemsetAsync(dres, 0, b_r, s);
+      cudaMemcpyAsync(dslots, p_sl, b_sl, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(dqs, p_q, b_q, cudaMemcpyHostToDevice, s);
+      const cudaError_t el = launch_multi(dslots, ctls, slots, dqs, hctl, dgraphs, dres, nullptr, M, blocks, s);
+      cudaMemcpyAsync(p_r, dres, b_r, cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(p_M2, M, sizeof(MCtl), cudaMemcpyDeviceToHost, s);
+      e = cudaStreamEndCapture(s, &graph);
+      if (e == cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+      cudaEventRecord(e0, s);
+      e = cudaGraphLaunch(exec, s);
+      cudaEventRecord(e1, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(e, "captured multi-query launch");
+    }
+    std::memcpy(hres.data(), p_r, b_r);
+    hM2 = *p_M2;
+  } else {
+    CK(cudaMemsetAsync(used, 0, 8, s));
+    CK(cudaMemcpyAsync(hctl, hc.data(), hc.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(M, &hM, sizeof(MCtl), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dgraphs, &g->dev, sizeof(GraphDev), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctls, 0, slots * sizeof(QCtl), s));
+    CK(cudaMemsetAsync(dres, 0, nq * sizeof(QResult), s));
+    CK(cudaMemcpyAsync(dslots, hslots.data(), slots * sizeof(MSlot), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dqs, qs.data(), nq * sizeof(MQuery), cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    cudaError_t e = launch_multi(dslots, ctls, slots, dqs, hctl, dgraphs, dres, nullptr, M, blocks, s);
+    cudaEventRecord(e1, s);
+    cudaError_t e2 =
+        e == cudaSuccess ? cudaMemcpyAsync(hres.data(), dres, nq * sizeof(QResult), cudaMemcpyDeviceToHost, s) : e;
+    if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(&hM2, M, sizeof(MCtl), cudaMemcpyDeviceToHost, s);
+    cudaError_t e3 = cudaStreamSynchronize(s);
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "multi-query launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "batch status copy");
+    if (e3 != cudaSuccess) return cuda_fail(e3, "multi-query kernel");
+  }
   if (hM2.error) return fail((int)hM2.error, "multi-query kernel stopped with error %u", hM2.error);
   const bool paths = !(o.flags & OPMOS_FLAG_NO_PATHS);
   const uint64_t total_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(

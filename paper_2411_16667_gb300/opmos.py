@@ -17,6 +17,7 @@ _lib = None
 
 OK, ERR_INVALID_ARG, ERR_OVERFLOW, ERR_OUT_OF_MEMORY, ERR_CAPACITY, ERR_BUDGET, ERR_TIMEOUT, ERR_CUDA, PENDING = range(9)
 FLAG_NO_PATHS = 1
+FLAG_GRAPH = 2
 MAX_D = 8
 
 EXPORTS = ("opmos_default_options", "opmos_device_count", "opmos_graph_create", "opmos_graph_destroy",

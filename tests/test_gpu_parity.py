@@ -273,6 +273,19 @@ def test_batch_equals_single(op):
         assert np.array_equal(res.costs, alone.costs)
 
 
+def test_batch_graph_capture_gives_the_same_fronts(op):
+    """OPMOS_FLAG_GRAPH: the launch captured into a CUDA graph and replayed."""
+    g, queries = synth.config4(2, nq=16)
+    G = op.opmos_graph.from_synth(g)
+    starts, goals = [s for s, _ in queries], [t for _, t in queries]
+    plain = op.opmos_solve_batch(G, starts, goals, window=128)
+    captured = op.opmos_solve_batch(G, starts, goals, window=128, flags=op.FLAG_GRAPH)
+    for (s, t), (sa, ra), (sb, rb) in zip(queries, plain, captured):
+        assert sa == sb == op.OK
+        assert np.array_equal(ra.costs, rb.costs)
+        check_front(g, s, t, rb.costs, rb.paths)
+
+
 def test_batch_with_duplicate_and_trivial_queries(op):
     g, q = synth.config1()
     G = op.opmos_graph.from_synth(g)
