@@ -419,14 +419,15 @@ int solve_one(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint
   QArena A{};
   layout_arena(g, D, pl, (char*)arena, &A);
   void* outp = nullptr;
-  if (int rc = g_out.get(kOutWords * 4 + 1024, &outp)) return rc;
+  const size_t header = 4 * 256 + sizeof(QCtl) + sizeof(QResult);  // counters, control block, result
+  if (int rc = g_out.get(kOutWords * 4 + header, &outp)) return rc;
   char* op = (char*)outp;
   unsigned long long* used = carve<unsigned long long>(op, 1);
   QCtl* C = carve<QCtl>(op, 1);
   QResult* R = carve<QResult>(op, 1);
   uint32_t* words = carve<uint32_t>(op, kOutWords);
   OutPool O{words, kOutWords, used};
-  CK(cudaMemsetAsync(outp, 0, 1024, s));
+  CK(cudaMemsetAsync(outp, 0, (size_t)((char*)words - (char*)outp), s));
 
   QParams P{};
   P.start = start;
@@ -694,7 +695,7 @@ extern "C" {
 void opmos_default_options(opmos_options* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
-  o->window = 1024;
+  o->window = 512;
   o->lanes_per_label = 8;
   o->tile = 32;
   o->delta = 1;

@@ -61,20 +61,21 @@ struct GraphDev {
   const uint32_t* rcost;    // d*m, cost of each reversed arc
 };
 
+// A counter alone in its 128-byte line: the hot counters of a query are hit
+// by atomics from every warp each step, and counters sharing a line would
+// serialise on it.
+template <class T>
+struct alignas(128) Hot {
+  T v;
+};
+
 // Per-query control block (global memory). Counters that the team reads after
 // a barrier are plain words; concurrent updates use atomics.
 struct QCtl {
   unsigned error;
   unsigned done;
   unsigned step;
-  unsigned n_labels;
-  unsigned open_count[2];
-  unsigned win_count;
-  unsigned cand_count;
-  unsigned touched_count;
-  unsigned merge_next;    // next touched node to merge (dynamic scheduling)
   unsigned theta;
-  unsigned plog_len;
   unsigned plog_snap;
   unsigned res_count;
   unsigned res_status;
@@ -83,16 +84,22 @@ struct QCtl {
   unsigned ps_build, ps_src, ps_mark_new, ps_nbuild;
   unsigned ps_shift[3];
   unsigned ps_nb;         // index buffer being built this step
-  unsigned long long min_key[2];  // lexicographic minimum (F0 << 32 | F1) of OPEN
-  unsigned long long f_words;
   unsigned long long res_off;    // costs (count*d) then path offsets (count+1)
   unsigned long long res_path;   // nodes (total) then arc ids (total - count)
   unsigned long long res_total;  // total path nodes
   unsigned long long t_start;
   unsigned long long stats[kNStat];
-  unsigned bar_count;
-  unsigned bar_gen;
-  unsigned pad[2];
+  Hot<unsigned> n_labels;
+  Hot<unsigned> open_count[2];
+  Hot<unsigned> win_count;
+  Hot<unsigned> cand_count;
+  Hot<unsigned> touched_count;
+  Hot<unsigned> merge_next;    // next touched node to merge (dynamic scheduling)
+  Hot<unsigned> plog_len;
+  Hot<unsigned long long> min_key[2];  // lexicographic minimum (F0 << 32 | F1) of OPEN
+  Hot<unsigned long long> f_words;
+  Hot<unsigned> bar_count;
+  Hot<unsigned> bar_gen;
 };
 
 // Pointers into one query's arena (one slot).
@@ -237,17 +244,17 @@ struct GridTeam {
     __shared__ unsigned s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-      const unsigned gen = ld_volatile(&C->bar_gen);
+      const unsigned gen = ld_volatile(&C->bar_gen.v);
       __threadfence();
-      const unsigned arrived = atomicAdd(&C->bar_count, 1u);
+      const unsigned arrived = atomicAdd(&C->bar_count.v, 1u);
       if (arrived == gridDim.x - 1) {
-        atomicExch(&C->bar_count, 0u);
+        atomicExch(&C->bar_count.v, 0u);
         __threadfence();
-        atomicAdd(&C->bar_gen, 1u);
+        atomicAdd(&C->bar_gen.v, 1u);
       } else {
         const unsigned long long t0 = globaltimer();
         unsigned spins = 0;
-        while (ld_volatile(&C->bar_gen) == gen) {
+        while (ld_volatile(&C->bar_gen.v) == gen) {
           if (++spins > 64) __nanosleep(64);
           if ((spins & 255u) == 0) {
             if (ld_volatile(&C->error) != 0) break;

@@ -179,7 +179,7 @@ struct Search {
         C->error = 0;
         C->done = 0;
         C->step = 0;
-        C->win_count = C->cand_count = C->touched_count = 0;
+        C->win_count.v = C->cand_count.v = C->touched_count.v = 0;
         C->theta = 0;
         C->plog_snap = 0;
         C->res_count = C->res_status = 0;
@@ -203,28 +203,28 @@ struct Search {
 #pragma unroll
       for (int k = 0; k < D; ++k) A.fpool[(size_t)k * tile] = 0;
       A.fpool[(size_t)D * tile] = 0;
-      C->f_words = (unsigned long long)(D + 1) * tile;
-      C->n_labels = 1;
-      C->plog_len = 0;
+      C->f_words.v = (unsigned long long)(D + 1) * tile;
+      C->n_labels.v = 1;
+      C->plog_len.v = 0;
       const uint32_t h0 = hk(0, s);
       const uint64_t key = ((uint64_t)h0 << 32) | (D > 1 ? hk(1, s) : 0u);
       // start == goal: P = {l_s}, nothing to search. h(s) = inf: goal unreachable.
       if (s != t && h0 != kInf) {
         A.okey[0][0] = key;
         A.oid[0][0] = 0;
-        C->open_count[0] = 1;
-        C->min_key[0] = key;
+        C->open_count[0].v = 1;
+        C->min_key[0].v = key;
       } else {
-        C->open_count[0] = 0;
-        C->min_key[0] = ~0ull;
+        C->open_count[0].v = 0;
+        C->min_key[0].v = ~0ull;
       }
       if (s == t) {
 #pragma unroll
         for (int k = 0; k < D; ++k) A.plog[(size_t)k * A.plog_cap] = 0;
-        C->plog_len = 1;
+        C->plog_len.v = 1;
       }
-      C->open_count[1] = 0;
-      C->min_key[1] = ~0ull;
+      C->open_count[1].v = 0;
+      C->min_key[1].v = ~0ull;
       C->f1span[0] = C->f1span[1] = 0;
       C->ps_cur = C->ps_count = C->ps_mark = C->ps_ntiles = 0;
       C->ps_build = C->ps_src = C->ps_mark_new = C->ps_nbuild = C->ps_nb = 0;
@@ -258,12 +258,12 @@ struct Search {
     const unsigned nxt = cur ^ 1u;
     if (threadIdx.x == 0 && S.span) atomicMax(&C->f1span[nxt], S.span);
     if (T.leader()) {
-      C->open_count[nxt] = 0;
-      C->min_key[nxt] = ~0ull;
-      C->win_count = 0;
-      C->cand_count = 0;
-      C->touched_count = 0;
-      C->merge_next = 0;
+      C->open_count[nxt].v = 0;
+      C->min_key[nxt].v = ~0ull;
+      C->win_count.v = 0;
+      C->cand_count.v = 0;
+      C->touched_count.v = 0;
+      C->merge_next.v = 0;
     }
     if (T.leader_block()) plan_p_index();
   }
@@ -287,7 +287,7 @@ struct Search {
   __device__ void plan_p_index() {
     __syncthreads();
     if (D < 2) return;
-    const unsigned plen = ld_volatile(&C->plog_len);
+    const unsigned plen = ld_volatile(&C->plog_len.v);
     const bool build = plen - C->ps_mark > 32u + C->ps_count / 16u && plen <= kPSMax;
     if (threadIdx.x == 0) S.pmax[0] = S.pmax[1] = S.pmax[2] = 0;
     __syncthreads();
@@ -429,7 +429,7 @@ struct Search {
       // Alg. 1 l.8: a goal label is not expanded; it goes to P (virtual node n)
       if (gl == 0) {
         const uint32_t vp = G.n;
-        const unsigned c = agg_inc(&C->cand_count);
+        const unsigned c = agg_inc(&C->cand_count.v);
         A.cnode[c] = vp;
         A.cparent[c] = A.lparent[id];
         A.cedge[c] = A.ledge[id];
@@ -437,7 +437,7 @@ struct Search {
         for (int k = 0; k < D; ++k) A.cg[(size_t)k * A.cand_cap + c] = g[k];
         const int old = atomicExch(&A.node_head[vp], (int)c);
         A.cnext[c] = old;
-        if (old == kNil) A.touched[agg_inc(&C->touched_count)] = vp;
+        if (old == kNil) A.touched[agg_inc(&C->touched_count.v)] = vp;
       }
       return;
     }
@@ -446,7 +446,7 @@ struct Search {
       const uint32_t v2 = __ldg(G.col + e);
       st[S_CAND]++;
       if (hk(0, v2) == kInf) continue;  // goal unreachable from v2
-      const unsigned c = agg_inc(&C->cand_count);
+      const unsigned c = agg_inc(&C->cand_count.v);
       A.cnode[c] = v2;
       A.cparent[c] = id;
       A.cedge[c] = e;
@@ -454,7 +454,7 @@ struct Search {
       for (int k = 0; k < D; ++k) A.cg[(size_t)k * A.cand_cap + c] = g[k] + __ldg(G.cost + (size_t)k * G.m + e);
       const int old = atomicExch(&A.node_head[v2], (int)c);
       A.cnext[c] = old;
-      if (old == kNil) A.touched[agg_inc(&C->touched_count)] = v2;
+      if (old == kNil) A.touched[agg_inc(&C->touched_count.v)] = v2;
     }
   }
 
@@ -470,14 +470,14 @@ struct Search {
     for (unsigned i = T.tid(); i < kNB; i += T.nthreads()) A.hist[nxt * kNB + i] = 0;
     if (T.leader()) {
       C->theta = bstar;
-      C->plog_snap = ld_volatile(&C->plog_len);
+      C->plog_snap = ld_volatile(&C->plog_len.v);
       C->f1span[cur] = 0;  // measured again by the next step's phase 1
     }
     const uint64_t* in = A.okey[cur];
     const uint32_t* in_id = A.oid[cur];
     uint64_t* out = A.okey[nxt];
     uint32_t* out_id = A.oid[nxt];
-    const unsigned plen = ld_volatile(&C->plog_len);
+    const unsigned plen = ld_volatile(&C->plog_len.v);
     const unsigned pcount = ld_volatile(&C->ps_count);
     const unsigned pmark = ld_volatile(&C->ps_mark);
     const unsigned pntiles = ld_volatile(&C->ps_ntiles);
@@ -527,7 +527,7 @@ struct Search {
         A.lstatus[id] = ST_DEAD;
         st[S_GOALPRUNED]++;
       } else if (want) {
-        if (agg_inc(&C->win_count) < A.win_cap) {
+        if (agg_inc(&C->win_count.v) < A.win_cap) {
           A.lstatus[id] = ST_CLOSED;
           st[S_EXTRACTED]++;
           take = true;
@@ -536,7 +536,7 @@ struct Search {
         }
       }
       if (keep) {
-        const unsigned o = agg_inc(&C->open_count[nxt]);
+        const unsigned o = agg_inc(&C->open_count[nxt].v);
         if (o < A.open_cap) {
           out[o] = key;
           out_id[o] = id;
@@ -555,7 +555,7 @@ struct Search {
     }
     if (lane == 0) st[S_PCMP] += pcmp;
     kmin = warp_min64(kmin);
-    if (lane == 0 && kmin != ~0ull) atomicMin(&C->min_key[nxt], kmin);
+    if (lane == 0 && kmin != ~0ull) atomicMin(&C->min_key[nxt].v, kmin);
     build_p_rank(T);
   }
 
@@ -666,7 +666,7 @@ struct Search {
       // P index and every goal cost logged since it was built (this warp is
       // the only writer of the log in this phase). P members a new solution
       // dominates are dropped once, at output (Prune(P, l) of l.11).
-      const unsigned plen = ld_volatile(&C->plog_len);
+      const unsigned plen = ld_volatile(&C->plog_len.v);
       p_filter(alive, c, pcount ? pmark : 0u, plen, pcount, pntiles, pbuf, pcmp);
     } else {
       // (b) against the frontier alpha(v), compacting it in place; four
@@ -743,7 +743,7 @@ struct Search {
     const unsigned ns = __popc(smask);
     if (ns) {
       unsigned lb = 0;
-      if (lane == 0) lb = atomicAdd(&C->n_labels, ns);
+      if (lane == 0) lb = atomicAdd(&C->n_labels.v, ns);
       lb = __shfl_sync(0xffffffffu, lb, 0);
       const bool over_budget = lb + ns > P.label_budget;
       if (lb + ns > A.label_cap || over_budget) {
@@ -756,7 +756,7 @@ struct Search {
           unsigned ncap = max(2u * need, tile);
           ncap = (ncap + tile - 1) / tile * tile;
           unsigned long long nb0 = 0;
-          if (lane == 0) nb0 = atomicAdd(&C->f_words, (unsigned long long)(D + 1) * ncap);
+          if (lane == 0) nb0 = atomicAdd(&C->f_words.v, (unsigned long long)(D + 1) * ncap);
           nb0 = __shfl_sync(0xffffffffu, nb0, 0);
           if (nb0 + (unsigned long long)(D + 1) * ncap > A.fpool_words) {
             if (lane == 0) set_error(C, OPMOS_ERR_CAPACITY);
@@ -775,7 +775,7 @@ struct Search {
         }
         unsigned plen = 0;
         if (is_goal) {
-          plen = ld_volatile(&C->plog_len);
+          plen = ld_volatile(&C->plog_len.v);
           if (plen + ns > A.plog_cap) {
             if (lane == 0) set_error(C, OPMOS_ERR_CAPACITY);
             return;
@@ -800,7 +800,7 @@ struct Search {
             for (int k = 0; k < D; ++k) A.plog[(size_t)k * A.plog_cap + plen + r] = c[k];
           } else {
             const uint64_t key = ((uint64_t)(c[0] + hk(0, v)) << 32) | (D > 1 ? c[1 % D] + hk(1 % D, v) : 0u);
-            const unsigned o = agg_inc(&C->open_count[nxt]);
+            const unsigned o = agg_inc(&C->open_count[nxt].v);
             if (o < A.open_cap) {
               A.okey[nxt][o] = key;
               A.oid[nxt][o] = id;
@@ -811,10 +811,10 @@ struct Search {
           }
         }
         my_key = warp_min64(my_key);
-        if (lane == 0 && my_key != ~0ull) atomicMin(&C->min_key[nxt], my_key);
+        if (lane == 0 && my_key != ~0ull) atomicMin(&C->min_key[nxt].v, my_key);
         if (is_goal && lane == 0) {
           __threadfence();
-          *reinterpret_cast<volatile unsigned*>(&C->plog_len) = plen + ns;
+          *reinterpret_cast<volatile unsigned*>(&C->plog_len.v) = plen + ns;
         }
         out += ns;
       }
@@ -830,7 +830,7 @@ struct Search {
 
   template <class Team>
   __device__ void phase_merge(const Team& T, unsigned cur) {
-    const unsigned nt = ld_volatile(&C->touched_count);
+    const unsigned nt = ld_volatile(&C->touched_count.v);
     const unsigned psnap = ld_volatile(&C->plog_snap);
     const unsigned pcount = ld_volatile(&C->ps_count);
     const unsigned pmark = ld_volatile(&C->ps_mark);
@@ -839,7 +839,7 @@ struct Search {
     const unsigned lane = lane_id();
     for (;;) {
       unsigned t = 0;
-      if (lane == 0) t = atomicAdd(&C->merge_next, 1u);
+      if (lane == 0) t = atomicAdd(&C->merge_next.v, 1u);
       t = __shfl_sync(0xffffffffu, t, 0);
       if (t >= nt) break;
       const uint32_t v = A.touched[t];
@@ -1040,10 +1040,10 @@ __device__ void run_query(const GraphDev& G, const QArena& A, QCtl* C, const QPa
   };
   while (ok) {
     const unsigned cur = step & 1u;
-    const unsigned n_in = ld_volatile(&C->open_count[cur]);
+    const unsigned n_in = ld_volatile(&C->open_count[cur].v);
     if (n_in == 0) break;
     if (T.leader() && globaltimer() - C->t_start > P.time_limit_ns) set_error(C, OPMOS_ERR_TIMEOUT);
-    const unsigned long long base = ld_volatile64(&C->min_key[cur]);
+    const unsigned long long base = ld_volatile64(&C->min_key[cur].v);
     BinParams bp;
     bp.b0 = (uint32_t)(base >> 32);
     bp.b1 = (uint32_t)base;
@@ -1068,7 +1068,7 @@ __device__ void run_query(const GraphDev& G, const QArena& A, QCtl* C, const QPa
     lap(S_TOUT);
   }
   X.st[S_STEPS] = T.leader() ? step : 0;
-  X.st[S_GOALINS] = T.leader() ? ld_volatile(&C->plog_len) : 0;
+  X.st[S_GOALINS] = T.leader() ? ld_volatile(&C->plog_len.v) : 0;
   flush_stats<Team>(C, X.st);
   T.sync(C);
   if (T.leader()) {
@@ -1078,8 +1078,8 @@ __device__ void run_query(const GraphDev& G, const QArena& A, QCtl* C, const QPa
     R->off = C->res_off;
     R->path = C->res_path;
     R->total = C->res_total;
-    R->labels = C->n_labels;
-    R->f_words = C->f_words;
+    R->labels = C->n_labels.v;
+    R->f_words = C->f_words.v;
     for (int i = 0; i < kNStat; ++i) R->stats[i] = C->stats[i];
   }
 }
@@ -1155,10 +1155,10 @@ __device__ void mq_write_result(const MSlot& sl, unsigned slot, QCtl* C, QResult
   R->off = C->res_off;
   R->path = C->res_path;
   R->total = C->res_total;
-  R->labels = C->n_labels;
-  R->f_words = C->f_words;
+  R->labels = C->n_labels.v;
+  R->f_words = C->f_words.v;
   C->stats[S_STEPS] = C->step;
-  C->stats[S_GOALINS] = C->plog_len;
+  C->stats[S_GOALINS] = C->plog_len.v;
   for (int i = 0; i < kNStat; ++i) R->stats[i] = C->stats[i];
   if (done_flags) {
     __threadfence_system();  // the record is visible before its completion flag
@@ -1191,7 +1191,7 @@ __device__ void mq_schedule(MSlot* slots, QCtl* ctls, unsigned nslots, const MQu
     if (st == SL_RUN) {
       const unsigned step = C->step + 1;
       C->step = step;
-      if (ld_volatile(&C->error) || ld_volatile(&C->open_count[step & 1u]) == 0)
+      if (ld_volatile(&C->error) || ld_volatile(&C->open_count[step & 1u].v) == 0)
         st = SL_OUT1;
       else if (globaltimer() - C->t_start > sl.P.time_limit_ns) {
         atomicCAS(&C->error, 0u, (unsigned)OPMOS_ERR_TIMEOUT);
@@ -1199,7 +1199,7 @@ __device__ void mq_schedule(MSlot* slots, QCtl* ctls, unsigned nslots, const MQu
       }
       if (st == SL_OUT1) C->res_count = 0;
     } else if (st == SL_INIT) {
-      st = (ld_volatile(&C->error) || ld_volatile(&C->open_count[0]) == 0) ? SL_OUT1 : SL_RUN;
+      st = (ld_volatile(&C->error) || ld_volatile(&C->open_count[0].v) == 0) ? SL_OUT1 : SL_RUN;
       if (st == SL_OUT1) C->res_count = 0;
     } else if (st == SL_OUT1 || st == SL_OUT2 || st == SL_OUT3 || st == SL_OUT4) {
       // one output part per iteration; an error ends the output early
@@ -1289,8 +1289,8 @@ __device__ void mq_work(MSlot* slots, QCtl* ctls, unsigned q, unsigned j, unsign
   } else if (st == SL_RUN) {
     const SubTeam T{j, nb};
     const unsigned cur = C->step & 1u;
-    const unsigned n_in = ld_volatile(&C->open_count[cur]);
-    const unsigned long long base = ld_volatile64(&C->min_key[cur]);
+    const unsigned n_in = ld_volatile(&C->open_count[cur].v);
+    const unsigned long long base = ld_volatile64(&C->min_key[cur].v);
     BinParams bp;
     bp.b0 = (uint32_t)(base >> 32);
     bp.b1 = (uint32_t)base;
@@ -1322,7 +1322,7 @@ __device__ __forceinline__ unsigned mq_weight(const MSlot& sl, QCtl* C, unsigned
   }
   if (st >= SL_OUT1) return ph == 1 ? max(1u, ld_volatile(&C->res_count) + A_fcount_goal(sl)) : 0u;
   const unsigned cur = C->step & 1u;
-  const unsigned w = ph == 3 ? ld_volatile(&C->touched_count) : ld_volatile(&C->open_count[cur]);
+  const unsigned w = ph == 3 ? ld_volatile(&C->touched_count.v) : ld_volatile(&C->open_count[cur].v);
   return w ? w : 1u;  // a running slot always gets a block (index builds run in every phase)
 }
 
