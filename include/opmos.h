@@ -6,10 +6,10 @@
  * cost vectors and one path per vector (problem statement, Sec. 3), by the
  * ordered-parallel label-setting search of Sec. 5 (Algorithm 2) on one GPU:
  * each step extracts the window of open labels with the lowest F = g + h in
- * lexicographic order, expands them along their out-arcs (Algorithm 1 lines
- * 15-17), and merges the candidates into the target nodes' frontiers and the
- * solution set P with dominance checks and pruning (Algorithm 1 lines 18-31,
- * lines 8-13 for the goal). The heuristic h is the ideal point: per objective,
+ * lexicographic order, expands them along their out-arcs (the expansion of
+ * Algorithm 1), and merges the candidates into the target nodes' frontiers
+ * and the solution set P with dominance checks and pruning (the frontier
+ * checks of Algorithm 1, and its goal branch for labels at the goal). The heuristic h is the ideal point: per objective,
  * the shortest distance from each node to the goal (Sec. 4).
  *
  * Conventions (all entry points):

@@ -12,12 +12,12 @@
 //   * dominance a >- b: a[i] <= b[i] for all i and a[i] < b[i] for some i (Sec. 3);
 //   * PruneOPEN(l) removes OPEN labels l* with g(l) <= F(l*) componentwise
 //     (the parenthetical in Sec. 3 prints the inequality reversed);
-//   * NotDominated against P (Alg. 1 lines 12, 19, 29) is taken as "no p in P
+//   * NotDominated against P (Algorithm 1, all three uses) is taken as "no p in P
 //     weakly dominates", which keeps P cost-unique as Sec. 3 requires;
 //   * OPEN ties in F are broken by label creation order;
 //   * Visited(v) := a label was ever inserted at v;
 //   * a candidate whose node has no path to the goal (h = infinity) is dropped;
-//   * goal labels are not expanded (Alg. 1 line 8 vs line 14).
+//   * goal labels are not expanded (Algorithm 1: the goal branch ends the iteration).
 // Arithmetic is uint64; results that do not fit uint32 are reported as overflow.
 // The heuristic is the ideal point: h_k(v) = single-objective shortest distance
 // from v to the goal under objective k (Sec. 4), by reverse Dijkstra.
@@ -125,15 +125,15 @@ struct Pool {
 };
 
 struct Counters {
-  uint64_t extracted = 0;        // OPEN.popmin calls (Alg. 1 line 6)
-  uint64_t goal_extracted = 0;   // of which at the goal (line 8)
-  uint64_t expanded = 0;         // labels whose neighbours were generated (line 15)
-  uint64_t candidates = 0;       // l' generated (line 16)
-  uint64_t inserted = 0;         // OPEN inserts (lines 20, 30), including l_s
-  uint64_t pruned_open = 0;      // OPEN labels removed by a frontier Prune (line 28)
-  uint64_t pruned_open_goal = 0; // OPEN labels removed by PruneOPEN (lines 9-10)
-  uint64_t pruned_closed = 0;    // G_CL labels removed (line 26)
-  uint64_t pruned_p = 0;         // P labels removed (line 11)
+  uint64_t extracted = 0;        // OPEN.popmin calls (Algorithm 1)
+  uint64_t goal_extracted = 0;   // of which at the goal
+  uint64_t expanded = 0;         // labels whose neighbours were generated
+  uint64_t candidates = 0;       // l' generated
+  uint64_t inserted = 0;         // OPEN inserts, including l_s
+  uint64_t pruned_open = 0;      // OPEN labels removed by Prune(G_OP(v'), l')
+  uint64_t pruned_open_goal = 0; // OPEN labels removed by PruneOPEN(l)
+  uint64_t pruned_closed = 0;    // G_CL labels removed by Prune(G_CL(v'), l')
+  uint64_t pruned_p = 0;         // P labels removed by Prune(P, l)
   uint64_t comparisons = 0;      // vector dominance/equality tests
   uint64_t max_open = 0;
   uint64_t ns = 0;               // main loop wall time, steady clock
@@ -236,25 +236,25 @@ struct Namoa {
 
   int run() {
     t0 = std::chrono::steady_clock::now();
-    // lines 3-4: l_s = (v_s, 0), into OPEN and G_OP(v_s)
+    // initialisation: l_s = (v_s, 0), into OPEN and G_OP(v_s)
     uint64_t zero[kMaxD] = {0}, Fs[kMaxD];
     for (int i = 0; i < d; ++i) Fs[i] = h_inf(start) ? kInf64 : hv(i, start);
     uint32_t ls;
     if (int rc = new_label(start, kNone, ~0ull, zero, Fs, &ls)) return rc;
     open_insert(ls);
-    // line 5
+    // main loop: while OPEN is not empty
     while (!open.empty()) {
-      // line 6: l <- OPEN.popmin()
+      // l <- OPEN.popmin()
       uint32_t l = *open.begin();
       open.erase(open.begin());
       cnt.extracted++;
       const uint32_t v = pool.node[l];
-      // line 7
+      // move l from G_OP(v) to G_CL(v)
       erase_id(gop[v], l);
       gcl[v].push_back(l);
       if (v == goal) {
         cnt.goal_extracted++;
-        // lines 9-10: PruneOPEN(l) over the whole OPEN
+        // goal branch: PruneOPEN(l) over the whole OPEN
         for (auto it = open.begin(); it != open.end();) {
           cnt.comparisons++;
           if (weakly(pool.g(l), pool.F(*it), d)) {
@@ -265,7 +265,7 @@ struct Namoa {
             ++it;
           }
         }
-        // line 11: Prune(P, l)
+        // Prune(P, l)
         for (size_t i = 0; i < P.size();) {
           cnt.comparisons++;
           if (dominates(pool.g(l), pool.g(P[i]), d)) {
@@ -275,15 +275,15 @@ struct Namoa {
             ++i;
           }
         }
-        // lines 12-13
+        // insert l into P unless a member weakly dominates it
         if (not_dominated_by_P(pool.g(l))) P.push_back(l);
         continue;
       }
-      // line 15
+      // expansion of l along the out-arcs of v
       cnt.expanded++;
       for (uint64_t e = G.rowptr[v]; e < G.rowptr[v + 1]; ++e) {
         const uint32_t vp = G.col[e];
-        // lines 16-17
+        // l' = (v', g + c(e)), F(l') = g(l') + h(v')
         cnt.candidates++;
         if (h_inf(vp)) continue;
         uint64_t g2[kMaxD], F2[kMaxD];
@@ -292,7 +292,7 @@ struct Namoa {
           F2[i] = g2[i] + hv(i, vp);
         }
         if (!visited[vp]) {
-          // lines 18-21
+          // v' never visited: insert l' unless P dominates F(l')
           if (not_dominated_by_P(F2)) {
             uint32_t id;
             if (int rc = new_label(vp, l, e, g2, F2, &id)) return rc;
@@ -300,7 +300,7 @@ struct Namoa {
           }
           continue;
         }
-        // lines 22-23: Duplicate(l')
+        // Duplicate(l')
         bool dup = false;
         for (const auto* S : {&gop[vp], &gcl[vp]})
           for (uint32_t x : *S) {
@@ -308,7 +308,7 @@ struct Namoa {
             if (equal(pool.g(x), g2, d)) dup = true;
           }
         if (dup) continue;
-        // lines 24-25: NotDominated(l', G_OP(v')) and NotDominated(l', G_CL(v'))
+        // NotDominated(l', G_OP(v')) and NotDominated(l', G_CL(v'))
         bool dominated = false;
         for (const auto* S : {&gop[vp], &gcl[vp]})
           for (uint32_t x : *S) {
@@ -316,7 +316,7 @@ struct Namoa {
             if (dominates(pool.g(x), g2, d)) dominated = true;
           }
         if (dominated) continue;
-        // line 26: Prune(G_CL(v'), l')
+        // Prune(G_CL(v'), l')
         for (size_t i = 0; i < gcl[vp].size();) {
           cnt.comparisons++;
           if (dominates(g2, pool.g(gcl[vp][i]), d)) {
@@ -326,7 +326,7 @@ struct Namoa {
             ++i;
           }
         }
-        // lines 27-28: Prune(G_OP(v'), l') and remove the pruned labels from OPEN
+        // Prune(G_OP(v'), l') and remove the pruned labels from OPEN
         for (size_t i = 0; i < gop[vp].size();) {
           cnt.comparisons++;
           if (dominates(g2, pool.g(gop[vp][i]), d)) {
@@ -337,7 +337,7 @@ struct Namoa {
             ++i;
           }
         }
-        // lines 29-31
+        // insert l' unless P dominates F(l')
         if (not_dominated_by_P(F2)) {
           uint32_t id;
           if (int rc = new_label(vp, l, e, g2, F2, &id)) return rc;

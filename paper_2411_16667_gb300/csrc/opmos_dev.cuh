@@ -9,9 +9,9 @@
 //              live entries (alpha(v) = G_OP(v) u G_CL(v), Sec. 3)
 //   OPEN       two unsorted arrays of 64-bit keys (F[0] << 32 | F[1]) with
 //              label ids beside them, bucketed through a per-step histogram
-//              (Algorithm 2 l.9-16): the lowest F[0] bucket is split by F[1]
+//              (the batch extraction of Algorithm 2): the lowest F[0] bucket is split by F[1]
 //   P log      append-only list of every goal cost vector ever accepted; its
-//              prefix is a valid filter for "F dominated by P" (Alg. 1 l.19/29)
+//              prefix is a valid filter for "F dominated by P" (Algorithm 1)
 //   P index    a snapshot of P sorted along a Z-order curve over objectives
 //              1..3, tiled by 32 with each tile's componentwise minimum
 #pragma once
@@ -28,6 +28,7 @@ constexpr int32_t kNil = -1;
 constexpr int kNB = 2048;   // open-list histogram buckets per step
 constexpr int kNB1 = 1024;  // of which sub-buckets (by F[1]) of the lowest F[0] bucket
 constexpr unsigned kPSMax = 32768;  // largest P indexed by the sorted snapshot
+constexpr unsigned kHeavyFrontier = 512;  // frontiers this large are merged by a whole block
 
 enum : uint8_t { ST_OPEN = 0, ST_CLOSED = 1, ST_DEAD = 2 };
 
@@ -95,6 +96,8 @@ struct QCtl {
   Hot<unsigned> cand_count;
   Hot<unsigned> touched_count;
   Hot<unsigned> merge_next;    // next touched node to merge (dynamic scheduling)
+  Hot<unsigned> heavy_count;   // touched nodes with a large frontier, merged by a whole block
+  Hot<unsigned> heavy_next;    // next heavy node to merge
   Hot<unsigned> plog_len;
   Hot<unsigned long long> min_key[2];  // lexicographic minimum (F0 << 32 | F1) of OPEN
   Hot<unsigned long long> f_words;

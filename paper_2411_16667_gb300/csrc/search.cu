@@ -4,26 +4,26 @@
 // of the search is four phases separated by team barriers:
 //
 //   1. histogram   the open entries by lexicographic bucket of (F[0], F[1])
-//                  (Algorithm 2 l.9: OPEN is a lexicographic priority queue):
+//                  (Algorithm 2: OPEN is a lexicographic priority queue):
 //                  one bucket per F[0] value, the lowest one split by F[1]
 //   2. extract     the window = every live entry in the lowest buckets whose
 //                  cumulative count stays within W (the NUM_POP of Sec. 5);
 //                  entries whose label was pruned are dropped here (lazy OPEN
-//                  delete, Sec. 5.1 / Alg. 2 l.11) and so are labels whose F is
-//                  weakly dominated by a solution (PruneOPEN, Alg. 1 l.9-10,
+//                  delete, Sec. 5.1 and Algorithm 2) and so are labels whose F is
+//                  weakly dominated by a solution (PruneOPEN of Algorithm 1,
 //                  applied lazily at extraction)
 //   3. expand      every window label along its out-arcs, L lanes per label:
-//                  g' = g + c(e), dropped if h(v') is infinite (Alg. 1 l.15-17)
+//                  g' = g + c(e), dropped if h(v') is infinite (Algorithm 1)
 //   4. merge       one warp per target node: the node's candidates of this step
 //                  are resolved against each other (in-batch dominance and
 //                  duplicates), then against the node's frontier alpha(v')
-//                  (Alg. 1 l.22-28: weakly dominated candidates are dropped,
+//                  (Algorithm 1: weakly dominated candidates are dropped,
 //                  strictly dominated frontier labels are pruned), then against
-//                  P on F (Alg. 1 l.29); survivors become labels, join alpha(v')
+//                  P on F (Algorithm 1); survivors become labels, join alpha(v')
 //                  and OPEN. Goal labels are ordinary labels until they are
-//                  extracted (Alg. 1 l.6-8); an extracted goal label is sent
+//                  extracted (Algorithm 1); an extracted goal label is sent
 //                  to a virtual node n that stands for P, whose merge applies
-//                  Alg. 1 l.11-13 and appends survivors to the P log.
+//                  the goal branch of Algorithm 1 and appends survivors to the P log.
 //
 // The F-against-P test of phase 4 uses an index of P rebuilt every time P has
 // grown by about 1/16: P sorted along a Z-order curve over objectives 1..3 in
@@ -99,6 +99,11 @@ struct Shared {
   unsigned f_min, b1_max;
   unsigned span;
   unsigned pmax[3];
+  // one batch of a heavy node's candidates, merged by the whole block
+  uint32_t mc[OPMOS_MAX_D][32];
+  int mmine[32];
+  int m_next;
+  unsigned m_nb, m_alive, m_kill, m_claim;
 };
 
 // Histogram bucket of an OPEN key (F0 << 32 | F1): buckets [0, kNB1) split the
@@ -157,8 +162,8 @@ struct Search {
     return __ldg(P.h + (size_t)k * G.n + v);
   }
 
-  // ---------------- initialisation (Algorithm 1 l.1-4) ----------------
-  // Empty frontiers and histograms (Alg. 1 l.1-2). The team must pass a
+  // ---------------- initialisation (Algorithm 1) ----------------
+  // Empty frontiers and histograms (the empty sets Algorithm 1 starts from). The team must pass a
   // barrier before init_seed writes the start node's frontier.
   template <class Team>
   __device__ void init_zero(const Team& T) {
@@ -171,7 +176,7 @@ struct Search {
     for (unsigned i = T.tid(); i < 2u * kNB; i += T.nthreads()) A.hist[i] = 0;
   }
 
-  // l_s = (v_s, 0) into OPEN and G_OP(v_s) (Alg. 1 l.3-4), control block reset.
+  // l_s = (v_s, 0) into OPEN and G_OP(v_s) (Algorithm 1), control block reset.
   template <class Team>
   __device__ void init_seed(const Team& T, bool reset_ctl) {
     if (T.leader()) {
@@ -180,6 +185,7 @@ struct Search {
         C->done = 0;
         C->step = 0;
         C->win_count.v = C->cand_count.v = C->touched_count.v = 0;
+        C->heavy_count.v = C->heavy_next.v = 0;
         C->theta = 0;
         C->plog_snap = 0;
         C->res_count = C->res_status = 0;
@@ -188,7 +194,7 @@ struct Search {
       }
       C->t_start = globaltimer();
       const uint32_t s = P.start, t = P.goal, tile = P.tile;
-      // l_s = (v_s, 0): label 0, frontier of v_s, OPEN (lines 3-4)
+      // l_s = (v_s, 0): label 0, frontier of v_s, OPEN
 #pragma unroll
       for (int k = 0; k < D; ++k) A.lg[(size_t)k * A.label_cap] = 0;
       A.lnode[0] = s;
@@ -264,6 +270,8 @@ struct Search {
       C->cand_count.v = 0;
       C->touched_count.v = 0;
       C->merge_next.v = 0;
+      C->heavy_count.v = 0;
+      C->heavy_next.v = 0;
     }
     if (T.leader_block()) plan_p_index();
   }
@@ -418,15 +426,15 @@ struct Search {
     return m ? __ffs(m) - 1 : 32u;
   }
 
-  // Expansion of one window label by the L lanes of a lane group (Algorithm 1
-  // l.15-17): g' = g + c(e) for every out-arc, dropped when h(v') is infinite.
+  // Expansion of one window label by the L lanes of a lane group (Algorithm
+  // 1): g' = g + c(e) for every out-arc, dropped when h(v') is infinite.
   __device__ void expand_label(uint32_t id, unsigned gl, unsigned L) {
     const uint32_t v = A.lnode[id];
     uint32_t g[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) g[k] = A.lg[(size_t)k * A.label_cap + id];
     if (v == P.goal) {
-      // Alg. 1 l.8: a goal label is not expanded; it goes to P (virtual node n)
+      // Algorithm 1: a goal label is not expanded; it goes to P (virtual node n)
       if (gl == 0) {
         const uint32_t vp = G.n;
         const unsigned c = agg_inc(&C->cand_count.v);
@@ -454,11 +462,18 @@ struct Search {
       for (int k = 0; k < D; ++k) A.cg[(size_t)k * A.cand_cap + c] = g[k] + __ldg(G.cost + (size_t)k * G.m + e);
       const int old = atomicExch(&A.node_head[v2], (int)c);
       A.cnext[c] = old;
-      if (old == kNil) A.touched[agg_inc(&C->touched_count.v)] = v2;
+      if (old == kNil) {
+        // a node with a large frontier is merged by a whole block; it is kept at
+        // the far end of the touched array (touched + heavy <= candidates <= cand_cap)
+        if (A.fcount[v2] >= kHeavyFrontier)
+          A.touched[A.cand_cap - 1u - atomicAdd(&C->heavy_count.v, 1u)] = v2;
+        else
+          A.touched[agg_inc(&C->touched_count.v)] = v2;
+      }
     }
   }
 
-  // ---------------- phase 2: extraction + expansion (Algorithm 2 l.9-16) ----------------
+  // ---------------- phase 2: extraction + expansion (Algorithm 2) ----------------
   // A warp reads 32 OPEN entries at a time: dead entries are dropped (lazy OPEN
   // delete), entries in the window whose F a solution weakly dominates are
   // dropped (lazy PruneOPEN), the other window entries are closed and expanded
@@ -560,7 +575,7 @@ struct Search {
   }
 
   // F against the P index + the recent goal costs log[t0, t1): clears alive
-  // for candidates a solution weakly dominates (Algorithm 1 l.19/29).
+  // for candidates a solution weakly dominates (Algorithm 1).
   __device__ void p_filter(bool& alive, const uint32_t (&F)[D], unsigned t0, unsigned t1, unsigned pcount,
                            unsigned pntiles, unsigned pbuf, unsigned long long& pcmp) {
     const unsigned lane = lane_id();
@@ -638,11 +653,10 @@ struct Search {
     }
   }
 
-  // ---------------- phase 4: merge (Algorithm 1 l.18-31, l.8-13) ----------------
+  // ---------------- phase 4: merge (Algorithm 1: frontier checks and goal branch) ----------------
   __device__ void merge_batch(uint32_t v, int mine, unsigned nb, unsigned cur, unsigned psnap, unsigned pmark,
                               unsigned pcount, unsigned pntiles, unsigned pbuf) {
     const unsigned lane = lane_id();
-    const unsigned nxt = cur ^ 1u;
     const bool is_goal = (v == G.n);  // the virtual node standing for P
     uint32_t c[D];
     const bool valid = lane < nb;
@@ -665,7 +679,7 @@ struct Search {
       // (b') at the goal alpha(v_g) is P: one weak-dominance test against the
       // P index and every goal cost logged since it was built (this warp is
       // the only writer of the log in this phase). P members a new solution
-      // dominates are dropped once, at output (Prune(P, l) of l.11).
+      // dominates are dropped once, at output (Prune(P, l) of Algorithm 1).
       const unsigned plen = ld_volatile(&C->plog_len.v);
       p_filter(alive, c, pcount ? pmark : 0u, plen, pcount, pntiles, pbuf, pcmp);
     } else {
@@ -730,13 +744,27 @@ struct Search {
           out += __popc(km);
         }
       }
-      // (c) F against P (Algorithm 1 l.29)
-      if (__any_sync(0xffffffffu, alive)) {
-        uint32_t F[D];
+    }
+    merge_finish(v, mine, c, valid, alive, out, fb, cap, cur, psnap, pmark, pcount, pntiles, pbuf, fcmp, pruned_n,
+                 pcmp);
+  }
+
+  // The end of a batch's merge, by one warp, lane j holding candidate j:
+  // (c) F against P (Algorithm 1) at an ordinary node, then (d) survivors
+  // become labels and join alpha(v) and OPEN (or the P log at the goal).
+  // out = live frontier entries left after (b); fb, cap = the frontier block.
+  __device__ void merge_finish(uint32_t v, int mine, const uint32_t (&c)[D], bool valid, bool alive, unsigned out,
+                               uint64_t fb, unsigned cap, unsigned cur, unsigned psnap, unsigned pmark,
+                               unsigned pcount, unsigned pntiles, unsigned pbuf, unsigned long long fcmp,
+                               unsigned long long pruned_n, unsigned long long pcmp) {
+    const unsigned lane = lane_id();
+    const unsigned nxt = cur ^ 1u;
+    const bool is_goal = (v == G.n);
+    if (!is_goal && __any_sync(0xffffffffu, alive)) {
+      uint32_t F[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) F[k] = c[k] + (valid ? hk(k, v) : 0u);
-        p_filter(alive, F, pcount ? pmark : 0u, psnap, pcount, pntiles, pbuf, pcmp);
-      }
+      for (int k = 0; k < D; ++k) F[k] = c[k] + (valid ? hk(k, v) : 0u);
+      p_filter(alive, F, pcount ? pmark : 0u, psnap, pcount, pntiles, pbuf, pcmp);
     }
     // (d) survivors become labels, join alpha(v), OPEN (or the P log at the goal)
     const unsigned smask = __ballot_sync(0xffffffffu, alive);
@@ -828,6 +856,159 @@ struct Search {
     }
   }
 
+  // Merge of a node with a large frontier by the whole block (every thread
+  // calls it). Batches of up to 32 candidates as in merge_batch; warp 0
+  // gathers a batch and resolves it in itself (a), then all warps scan the
+  // frontier (b) in rounds of nwarps * 32 * U entries, each warp U tiles of
+  // 32, and compact it in place: a round's reads all precede the first
+  // barrier, its writes land below the round's start, so they never overwrite
+  // an entry another warp still has to read. Candidates killed by one warp
+  // are dropped by the others from the next round on. A candidate that a
+  // frontier entry weakly dominates never dominates another entry (the
+  // frontier is an antichain), so the entries each candidate prunes do not
+  // depend on when its death is seen. Warp 0 then runs (c)-(d).
+  __device__ void merge_heavy(uint32_t v, unsigned cur, unsigned psnap, unsigned pmark, unsigned pcount,
+                              unsigned pntiles, unsigned pbuf) {
+    constexpr int U = 2;
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) {
+      S.m_next = A.node_head[v];
+      A.node_head[v] = kNil;
+    }
+    for (;;) {
+      __syncthreads();
+      if (S.m_next == kNil) break;
+      __syncthreads();  // every thread has read m_next before warp 0 moves it
+      if (w == 0) {
+        int cur_c = S.m_next;
+        int mine = kNil;
+        unsigned nb = 0;
+        while (cur_c != kNil && nb < 32) {
+          if (lane == nb) mine = cur_c;
+          cur_c = A.cnext[cur_c];
+          ++nb;
+        }
+        const bool valid = lane < nb;
+        uint32_t c[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) c[k] = valid ? A.cg[(size_t)k * A.cand_cap + mine] : 0u;
+        bool alive = valid;
+        for (unsigned j = 0; j < nb; ++j) {
+          uint32_t cj[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) cj[k] = __shfl_sync(0xffffffffu, c[k], j);
+          if (alive && lane != j && (dominates<D>(cj, c) || (j < lane && equal<D>(cj, c)))) alive = false;
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) S.mc[k][lane] = c[k];
+        S.mmine[lane] = mine;
+        const unsigned a0 = __ballot_sync(0xffffffffu, alive);
+        if (lane == 0) {
+          S.m_next = cur_c;
+          S.m_nb = nb;
+          S.m_alive = a0;
+          S.m_kill = 0;
+        }
+      }
+      __syncthreads();
+      unsigned a = S.m_alive;
+      const uint64_t fb = A.fbase[v];
+      const unsigned cap = A.fcap[v];
+      const unsigned fc = A.fcount[v];
+      unsigned out = 0;
+      unsigned long long fcmp = 0, pruned_n = 0;
+      const unsigned R = nw * 32u * U;
+      for (unsigned r0 = 0; r0 < fc; r0 += R) {
+        const unsigned base = r0 + w * 32u * U;
+        uint32_t m[U][D];
+        uint32_t mid[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const unsigned i = base + u * 32 + lane;
+          const bool vm = i < fc;
+#pragma unroll
+          for (int k = 0; k < D; ++k) m[u][k] = vm ? A.fpool[fb + (size_t)k * cap + i] : kInf;
+          mid[u] = vm ? A.fpool[fb + (size_t)D * cap + i] : 0u;
+        }
+        unsigned kill = 0, km[U], wtot = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const unsigned i0 = base + u * 32;
+          const unsigned i = i0 + lane;
+          const bool vm = i < fc;
+          bool pruned = false;
+          unsigned am = i0 < fc ? (a & ~kill) : 0u;
+          if (i0 < fc) fcmp += (unsigned long long)__popc(am) * min(32u, fc - i0);
+          while (am) {
+            const unsigned j = __ffs(am) - 1;
+            am &= am - 1;
+            uint32_t cj[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) cj[k] = S.mc[k][j];
+            if (__ballot_sync(0xffffffffu, vm && weakly_le<D>(m[u], cj))) kill |= 1u << j;
+            pruned |= vm && dominates<D>(cj, m[u]);
+          }
+          if (vm && pruned) {
+            A.lstatus[mid[u]] = ST_DEAD;
+            pruned_n++;
+          }
+          km[u] = __ballot_sync(0xffffffffu, vm && !pruned);
+          wtot += __popc(km[u]);
+        }
+        if (lane == 0) {
+          S.warp[w] = wtot;
+          if (kill) atomicOr(&S.m_kill, kill);
+        }
+        __syncthreads();  // (1) all reads of this round are done
+        const unsigned x = lane < nw ? S.warp[lane] : 0u;
+        unsigned incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= (unsigned)o) incl += y;
+        }
+        const unsigned wpre = __shfl_sync(0xffffffffu, incl - x, w);
+        const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+        a &= ~S.m_kill;
+        unsigned pos = out + wpre;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const unsigned i = base + u * 32 + lane;
+          const bool keep = (km[u] >> lane) & 1u;
+          const unsigned p = pos + __popc(km[u] & lanemask_lt());
+          if (keep && p != i) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) A.fpool[fb + (size_t)k * cap + p] = m[u][k];
+            A.fpool[fb + (size_t)D * cap + p] = mid[u];
+          }
+          pos += __popc(km[u]);
+        }
+        __syncthreads();  // (2) S.warp and S.m_kill read by every warp
+        const unsigned seen = min(r0 + R, fc);
+        out += total;
+        if (a == 0 && out == seen) {
+          // no candidate left to test and nothing moved: the rest stays in place
+          out = fc;
+          break;
+        }
+      }
+      if (lane == 0) {
+        st[S_PRUNED] += pruned_n;
+        st[S_FCMP] += fcmp;
+      }
+      if (w == 0) {
+        const unsigned nb = S.m_nb;
+        const bool valid = lane < nb;
+        uint32_t c[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) c[k] = S.mc[k][lane];
+        const bool alive = valid && ((a >> lane) & 1u);
+        merge_finish(v, S.mmine[lane], c, valid, alive, out, fb, cap, cur, psnap, pmark, pcount, pntiles, pbuf,
+                     0ull, 0ull, 0ull);
+      }
+    }
+  }
+
   template <class Team>
   __device__ void phase_merge(const Team& T, unsigned cur) {
     const unsigned nt = ld_volatile(&C->touched_count.v);
@@ -837,6 +1018,16 @@ struct Search {
     const unsigned pntiles = ld_volatile(&C->ps_ntiles);
     const unsigned pbuf = ld_volatile(&C->ps_cur);
     const unsigned lane = lane_id();
+    // heavy nodes first, one block each
+    const unsigned nh = ld_volatile(&C->heavy_count.v);
+    while (nh) {
+      if (threadIdx.x == 0) S.m_claim = atomicAdd(&C->heavy_next.v, 1u);
+      __syncthreads();
+      const unsigned h = S.m_claim;
+      __syncthreads();
+      if (h >= nh) break;
+      merge_heavy(A.touched[A.cand_cap - 1u - h], cur, psnap, pmark, pcount, pntiles, pbuf);
+    }
     for (;;) {
       unsigned t = 0;
       if (lane == 0) t = atomicAdd(&C->merge_next.v, 1u);
@@ -1322,7 +1513,8 @@ __device__ __forceinline__ unsigned mq_weight(const MSlot& sl, QCtl* C, unsigned
   }
   if (st >= SL_OUT1) return ph == 1 ? max(1u, ld_volatile(&C->res_count) + A_fcount_goal(sl)) : 0u;
   const unsigned cur = C->step & 1u;
-  const unsigned w = ph == 3 ? ld_volatile(&C->touched_count.v) : ld_volatile(&C->open_count[cur].v);
+  const unsigned w = ph == 3 ? ld_volatile(&C->touched_count.v) + 8u * ld_volatile(&C->heavy_count.v)
+                             : ld_volatile(&C->open_count[cur].v);
   return w ? w : 1u;  // a running slot always gets a block (index builds run in every phase)
 }
 
