@@ -197,7 +197,7 @@ int plan_arena(const opmos_graph* g, uint32_t D, uint32_t window, size_t budget,
   pl->cand_cap = pl->win_cap * std::max<uint32_t>(g->maxdeg, 1);
   pl->plog_cap = batch ? (1u << 16) : (1u << 20);
   const size_t ptiles = pl->plog_cap / 32 + 1;
-  size_t fixed = (n + 1) * (8 + 4 + 4 + 4) + 2 * kNB * 4 + (size_t)pl->win_cap * 4 +
+  size_t fixed = (n + 1) * (8 + 4 + 4 + 4 + 4 + 4 * kNodeSlots) + 2 * kNB * 4 + (size_t)pl->win_cap * 4 +
                  (size_t)pl->cand_cap * (16 + 4 * D + 4) + (size_t)pl->plog_cap * 4 * D +
                  2 * ((size_t)pl->plog_cap + ptiles) * 4 * D + 64 * 256;
   if (budget < fixed + (8u << 20))
@@ -221,6 +221,8 @@ void layout_arena(const opmos_graph* g, uint32_t D, const ArenaPlan& pl, char* b
   A->fcount = carve<uint32_t>(p, n);
   A->fcap = carve<uint32_t>(p, n);
   A->node_head = carve<int32_t>(p, n);
+  A->ncand = carve<uint32_t>(p, n);
+  A->cslot = carve<int32_t>(p, n * kNodeSlots);
   A->hist = carve<uint32_t>(p, 2 * kNB);
   A->window = carve<uint32_t>(p, pl.win_cap);
   A->cnode = carve<uint32_t>(p, pl.cand_cap);

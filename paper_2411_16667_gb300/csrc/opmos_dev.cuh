@@ -29,6 +29,7 @@ constexpr int kNB = 2048;   // open-list histogram buckets per step
 constexpr int kNB1 = 1024;  // of which sub-buckets (by F[1]) of the lowest F[0] bucket
 constexpr unsigned kPSMax = 32768;  // largest P indexed by the sorted snapshot
 constexpr unsigned kHeavyFrontier = 512;  // frontiers this large are merged by a whole block
+constexpr unsigned kNodeSlots = 32;  // candidates a node holds in slots per step; more go to a list
 
 enum : uint8_t { ST_OPEN = 0, ST_CLOSED = 1, ST_DEAD = 2 };
 
@@ -110,7 +111,9 @@ struct QArena {
   uint64_t* fbase;     // n
   uint32_t* fcount;    // n
   uint32_t* fcap;      // n
-  int32_t* node_head;  // n
+  int32_t* node_head;  // n: this step's candidates beyond the slots (linked by cnext)
+  uint32_t* ncand;     // n: candidates that reached the node this step
+  int32_t* cslot;      // n * kNodeSlots: the first kNodeSlots of them
   uint32_t* lg;        // d * label_cap
   uint32_t* lnode;
   uint32_t* lparent;

@@ -172,6 +172,7 @@ struct Search {
       A.fcap[v] = 0;
       A.fbase[v] = 0;
       A.node_head[v] = kNil;
+      A.ncand[v] = 0;
     }
     for (unsigned i = T.tid(); i < 2u * kNB; i += T.nthreads()) A.hist[i] = 0;
   }
@@ -443,9 +444,12 @@ struct Search {
         A.cedge[c] = A.ledge[id];
 #pragma unroll
         for (int k = 0; k < D; ++k) A.cg[(size_t)k * A.cand_cap + c] = g[k];
-        const int old = atomicExch(&A.node_head[vp], (int)c);
-        A.cnext[c] = old;
-        if (old == kNil) A.touched[agg_inc(&C->touched_count.v)] = vp;
+        const unsigned pos = atomicAdd(&A.ncand[vp], 1u);
+        if (pos < kNodeSlots)
+          A.cslot[(size_t)vp * kNodeSlots + pos] = (int)c;
+        else
+          A.cnext[c] = atomicExch(&A.node_head[vp], (int)c);
+        if (pos == 0) A.touched[agg_inc(&C->touched_count.v)] = vp;
       }
       return;
     }
@@ -460,9 +464,12 @@ struct Search {
       A.cedge[c] = e;
 #pragma unroll
       for (int k = 0; k < D; ++k) A.cg[(size_t)k * A.cand_cap + c] = g[k] + __ldg(G.cost + (size_t)k * G.m + e);
-      const int old = atomicExch(&A.node_head[v2], (int)c);
-      A.cnext[c] = old;
-      if (old == kNil) {
+      const unsigned pos = atomicAdd(&A.ncand[v2], 1u);
+      if (pos < kNodeSlots)
+        A.cslot[(size_t)v2 * kNodeSlots + pos] = (int)c;
+      else
+        A.cnext[c] = atomicExch(&A.node_head[v2], (int)c);
+      if (pos == 0) {
         // a node with a large frontier is merged by a whole block; it is kept at
         // the far end of the touched array (touched + heavy <= candidates <= cand_cap)
         if (A.fcount[v2] >= kHeavyFrontier)
@@ -871,10 +878,7 @@ struct Search {
                               unsigned pntiles, unsigned pbuf) {
     constexpr int U = 2;
     const unsigned lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) {
-      S.m_next = A.node_head[v];
-      A.node_head[v] = kNil;
-    }
+    if (threadIdx.x == 0) S.m_next = -2;  // first batch: the node's slots
     for (;;) {
       __syncthreads();
       if (S.m_next == kNil) break;
@@ -883,10 +887,23 @@ struct Search {
         int cur_c = S.m_next;
         int mine = kNil;
         unsigned nb = 0;
-        while (cur_c != kNil && nb < 32) {
-          if (lane == nb) mine = cur_c;
-          cur_c = A.cnext[cur_c];
-          ++nb;
+        if (cur_c == -2) {
+          const unsigned ncand = A.ncand[v];
+          const int slot = A.cslot[(size_t)v * kNodeSlots + lane];
+          cur_c = ncand > kNodeSlots ? A.node_head[v] : kNil;
+          __syncwarp();
+          if (lane == 0) {
+            A.ncand[v] = 0;
+            if (ncand > kNodeSlots) A.node_head[v] = kNil;
+          }
+          nb = min(ncand, kNodeSlots);
+          if (lane < nb) mine = slot;
+        } else {
+          while (cur_c != kNil && nb < 32) {
+            if (lane == nb) mine = cur_c;
+            cur_c = A.cnext[cur_c];
+            ++nb;
+          }
         }
         const bool valid = lane < nb;
         uint32_t c[D];
@@ -1034,9 +1051,18 @@ struct Search {
       t = __shfl_sync(0xffffffffu, t, 0);
       if (t >= nt) break;
       const uint32_t v = A.touched[t];
-      int cur_c = A.node_head[v];
+      // the first kNodeSlots candidates sit in the node's slots (one load), the
+      // rest in a list
+      const unsigned ncand = A.ncand[v];
+      const int slot = A.cslot[(size_t)v * kNodeSlots + lane];
+      int cur_c = ncand > kNodeSlots ? A.node_head[v] : kNil;
       __syncwarp();
-      if (lane == 0) A.node_head[v] = kNil;
+      if (lane == 0) {
+        A.ncand[v] = 0;
+        if (ncand > kNodeSlots) A.node_head[v] = kNil;
+      }
+      const unsigned n0 = min(ncand, kNodeSlots);
+      merge_batch(v, lane < n0 ? slot : kNil, n0, cur, psnap, pmark, pcount, pntiles, pbuf);
       while (cur_c != kNil) {
         int mine = kNil;
         unsigned nb = 0;
