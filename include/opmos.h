@@ -70,7 +70,7 @@ typedef struct opmos_server opmos_server;
 typedef struct opmos_options {
   uint32_t window;           /* W: target number of labels extracted per step (the NUM_POP of
                                 Algorithm 2, Sec. 5). Steps take whole F[0] buckets, so a step
-                                may take fewer (never more than 4W). Default 512 (single query),
+                                may take fewer (never more than 4W). Default 1024 (single query),
                                 256 (batch). */
   uint32_t lanes_per_label;  /* threads that expand one label's out-arcs: 4, 8, 16 or 32.
                                 Default 8. */

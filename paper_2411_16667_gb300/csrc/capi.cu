@@ -697,7 +697,7 @@ extern "C" {
 void opmos_default_options(opmos_options* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
-  o->window = 512;
+  o->window = 1024;
   o->lanes_per_label = 8;
   o->tile = 32;
   o->delta = 1;

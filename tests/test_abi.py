@@ -30,7 +30,7 @@ def test_library_builds_and_exports_every_symbol():
 
 def test_options_struct_matches_defaults():
     o = opmos.opmos_default_options()
-    assert (o.window, o.lanes_per_label, o.tile, o.delta) == (512, 8, 32, 1)
+    assert (o.window, o.lanes_per_label, o.tile, o.delta) == (1024, 8, 32, 1)
     assert o.mem_budget_bytes == 8 << 30
     assert ctypes.sizeof(opmos.Options) == 48
     assert ctypes.sizeof(opmos.Stats) == 18 * 8

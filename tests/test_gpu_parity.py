@@ -296,3 +296,48 @@ def test_batch_with_duplicate_and_trivial_queries(op):
     assert np.array_equal(out[1][1].costs, exp)
     assert out[2][1].costs.tolist() == [[0, 0]]
     _same_front(out[3][1], oracle.solve(g, 5, 900).costs)
+
+
+# ---------------------------------------------------------------------------
+# config 3: 200k-node road-like graph, 4 objectives
+# ---------------------------------------------------------------------------
+def test_config3_road_graph_against_oracle(op):
+    """Every query among the first 16 that the oracle finishes within 300k
+    labels on the first two objectives, plus query 4 on the first three; each
+    alone and all together in one batch launch. (At d=4 the probed queries
+    exceed any label budget the oracle can meet in a test.)"""
+    g, queries = synth.config3()
+    G = op.opmos_graph.from_synth(g)
+    cases = []
+    for d, idx in ((2, range(16)), (3, [4])):
+        gd = g.first_objectives(d)
+        for i in idx:
+            s, t = queries[i]
+            f = oracle.solve(gd, s, t, label_budget=300_000, partial_ok=True)
+            if not f.stats["partial"]:
+                cases.append((d, s, t, f.costs))
+    assert sum(1 for c in cases if c[0] == 2) >= 4 and any(c[0] == 3 for c in cases)
+    for d, s, t, exp in cases:
+        res = op.opmos_solve(G, s, t, d_used=d)
+        _same_front(res, exp)
+        check_front(g.first_objectives(d), s, t, res.costs, res.paths)
+    two = [c for c in cases if c[0] == 2]
+    out = op.opmos_solve_batch(G, [c[1] for c in two], [c[2] for c in two], d_used=2)
+    for (d, s, t, exp), (st, res) in zip(two, out):
+        assert st == op.OK, f"query {s}->{t} status {st}"
+        _same_front(res, exp)
+
+
+def test_config3_full_d_batch_under_label_budget(op):
+    """All four objectives, 32 queries in one launch with a per-query label
+    budget (the time-limit practice of Sec. 6.1): each query ends OK with a
+    valid front or is reported as over budget; none fails otherwise."""
+    g, queries = synth.config3()
+    G = op.opmos_graph.from_synth(g)
+    qs = queries[:32]
+    out = op.opmos_solve_batch(G, [s for s, _ in qs], [t for _, t in qs], label_budget=200_000)
+    assert len(out) == len(qs)
+    for (s, t), (st, res) in zip(qs, out):
+        assert st in (op.OK, op.ERR_BUDGET), f"query {s}->{t} status {st}"
+        if st == op.OK:
+            check_front_sampled(g, s, t, res.costs, res.paths)
