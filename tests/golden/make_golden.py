@@ -2,6 +2,8 @@
 
 Usage: python tests/golden/make_golden.py config2 [--seed 1]
        python tests/golden/make_golden.py config4 --digests --jobs 6
+       python tests/golden/make_golden.py config3 --digests --shortest-hops 8 \
+              --budget 5000000 --jobs 8
 
 Only the oracle (Algorithm 1, ``oracle/``) and the input generators
 (``synth``) are called. Each fixture records the graph digest so a test can
@@ -20,7 +22,9 @@ Digest format (``--digests``; one line per query of the config):
     <qi> <start> <goal> <count> <labels> <extracted> <sha256 of the sorted
     front as little-endian uint32, first 16 hex digits>
 A query the oracle cannot finish within ``--budget`` labels is written with
-count -1.
+count -1. ``--shortest-hops K`` restricts the digests to the K queries with
+the fewest hops between start and goal (breadth-first search, ties by query
+index): the queries most likely to finish at full d.
 """
 from __future__ import annotations
 
@@ -75,23 +79,42 @@ def _digest_job(args):
             f"{front_digest(f.costs)}")
 
 
+def shortest_hop_queries(g, queries, k):
+    """Indices of the k queries with the fewest hops from start to goal."""
+    import numpy as np
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import shortest_path
+    a = sp.csr_matrix((np.ones(len(g.col)), g.col.astype(np.int64), g.rowptr.astype(np.int64)),
+                      shape=(g.n, g.n))
+    hops = []
+    for lo in range(0, len(queries), 32):
+        part = queries[lo:lo + 32]
+        dist = shortest_path(a, unweighted=True, indices=[s for s, _ in part])
+        hops += [int(dist[j, t]) for j, (_, t) in enumerate(part)]
+    return sorted(sorted(range(len(queries)), key=lambda i: (hops[i], i))[:k])
+
+
 def write_digests(args):
     g, queries = getattr(synth, args.config)(args.seed)
     if args.d:
         g = g.first_objectives(args.d)
-    jobs = [(args.config, args.seed, args.d, args.budget, qi) for qi in range(len(queries))]
+    sel = shortest_hop_queries(g, queries, args.shortest_hops) if args.shortest_hops else range(len(queries))
+    jobs = [(args.config, args.seed, args.d, args.budget, qi) for qi in sel]
     ctx = mp.get_context("spawn")
-    lines = [None] * len(jobs)
+    found = {}
     with ctx.Pool(args.jobs) as pool:
         for line in pool.imap_unordered(_digest_job, jobs):
-            lines[int(line.split()[0])] = line
-            done = sum(x is not None for x in lines)
-            if done % 64 == 0:
-                print(f"{done}/{len(jobs)} queries", flush=True)
+            found[int(line.split()[0])] = line
+            if len(found) % 64 == 0 or args.shortest_hops:
+                print(f"{len(found)}/{len(jobs)} queries", flush=True)
+    lines = [found[qi] for qi in sel]
     suffix = f"_d{args.d}" if args.d else ""
+    if args.shortest_hops:
+        suffix += f"_short{args.shortest_hops}"
     path = os.path.join(HERE, f"{args.config}_seed{args.seed}{suffix}.digests")
     with open(path + ".tmp", "w") as f:
-        f.write(f"# oracle fronts (Algorithm 1) as digests; label budget {args.budget or 'none'}\n")
+        f.write(f"# oracle fronts (Algorithm 1) as digests; label budget {args.budget or 'none'}"
+                + (f"; the {args.shortest_hops} shortest-hop queries" if args.shortest_hops else "") + "\n")
         f.write(f"graph {g.name} {g.digest()}\n")
         f.write("# qi start goal count labels extracted sha256[:16]\n")
         for line in lines:
@@ -109,6 +132,7 @@ def main():
     ap.add_argument("--digests", action="store_true", help="all queries, digest lines")
     ap.add_argument("--jobs", type=int, default=4)
     ap.add_argument("--budget", type=int, default=0, help="oracle label budget per query")
+    ap.add_argument("--shortest-hops", type=int, default=0, help="digests of the K fewest-hop queries only")
     args = ap.parse_args()
     if args.digests:
         write_digests(args)
