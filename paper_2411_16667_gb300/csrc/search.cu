@@ -26,10 +26,11 @@
 //                  the goal branch of Algorithm 1 and appends survivors to the P log.
 //
 // The F-against-P test of phase 4 uses an index of P rebuilt every time P has
-// grown by about 1/16: P sorted along a Z-order curve over objectives 1..3 in
-// tiles of 32, each with its componentwise minimum; a candidate only scans the
-// tiles whose minimum weakly dominates it, plus the goal costs found since the
-// last rebuild (the rebuild is split over phases 1-3 of a step).
+// grown by 32 + 1/64 of its indexed count: P sorted along a Z-order curve over
+// objectives 1..3 in tiles of 32, each with its componentwise minimum; a
+// candidate only scans the tiles whose minimum weakly dominates it, plus the
+// goal costs found since the last rebuild (the rebuild is split over phases
+// 1-3 of a step).
 //
 // A node is only ever touched by one warp per step, so frontier updates need
 // no locks. All waits are bounded (see GridTeam::sync).
@@ -290,14 +291,15 @@ struct Search {
     }
   }
 
-  // Decide whether this step rebuilds the P index (the P log grew by ~1/8
-  // since the last build) and fix the per-objective shifts that balance the
+  // Decide whether this step rebuilds the P index (the P log grew by 32 +
+  // 1/64 of the indexed count since the last build: every candidate scans
+  // the unindexed tail, a rebuild costs one O(k^2) rank pass) and fix the per-objective shifts that balance the
   // Z-order. The index covers log[0, mark); the rest is scanned directly.
   __device__ void plan_p_index() {
     __syncthreads();
     if (D < 2) return;
     const unsigned plen = ld_volatile(&C->plog_len.v);
-    const bool build = plen - C->ps_mark > 32u + C->ps_count / 16u && plen <= kPSMax;
+    const bool build = plen - C->ps_mark > 32u + C->ps_count / 64u && plen <= kPSMax;
     if (threadIdx.x == 0) S.pmax[0] = S.pmax[1] = S.pmax[2] = 0;
     __syncthreads();
     if (!build) return;
