@@ -9,8 +9,9 @@
  * lexicographic order, expands them along their out-arcs (the expansion of
  * Algorithm 1), and merges the candidates into the target nodes' frontiers
  * and the solution set P with dominance checks and pruning (the frontier
- * checks of Algorithm 1, and its goal branch for labels at the goal). The heuristic h is the ideal point: per objective,
- * the shortest distance from each node to the goal (Sec. 4).
+ * checks of Algorithm 1, and its goal branch for labels at the goal). The
+ * heuristic h is the ideal point: per objective, the shortest distance from
+ * each node to the goal (Sec. 4).
  *
  * Conventions (all entry points):
  *   - Every array argument is a HOST pointer. The library copies what it needs;
