@@ -60,21 +60,28 @@ CPU_SAMPLE_LABELS = 1_500_000
 
 # DRAM bytes (read + write) of one search_grid_kernel launch of the default
 # workload, from one ncu capture (profiles/search_grid_kernel_ship256-d3_dram.md),
-# valid only for the kernel sources whose digest is recorded beside it: once
-# the sources change the figure is reported as null until it is captured again.
-TRAFFIC = {"src_digest": "6a6ba87ef2585f3a", "bytes_per_launch": 303563520 + 695649792}
+# valid only for the kernel sources and launch options whose digest is recorded
+# beside it: once either changes the figure is reported as null until it is
+# captured again.
+TRAFFIC = {"src_digest": "cfa52670abb65fa5", "bytes_per_launch": 303563520 + 695649792}
 
 
-def kernel_source_digest() -> str:
-    """sha256 over the CUDA sources of the library (names and contents)."""
+# the translation unit of the search kernels: the file and every header it includes
+KERNEL_SOURCES = ("paper_2411_16667_gb300/csrc/search.cu", "paper_2411_16667_gb300/csrc/search.cuh",
+                  "paper_2411_16667_gb300/csrc/opmos_dev.cuh", "include/opmos.h")
+
+
+def kernel_source_digest(launch=()) -> str:
+    """sha256 over the search kernel's sources (names and contents) and the
+    launch options (window, lanes per label, tile, delta): what the kernel's
+    DRAM traffic on a given workload depends on."""
     import hashlib
-    d = os.path.join(ROOT, "paper_2411_16667_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(name.encode())
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(f.read())
+    for rel in KERNEL_SOURCES:
+        h.update(rel.encode())
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    h.update(repr(tuple(int(x) for x in launch)).encode())
     return h.hexdigest()[:16]
 
 
@@ -104,6 +111,52 @@ def cpu_sample(g, s, t, budget=CPU_SAMPLE_LABELS) -> dict:
     return {"value": st["extracted"] / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"sequential NAMOA* (Algorithm 1) on the same query, stopped at {budget} labels "
                       f"({st['extracted']} extracted in {secs:.2f} s main loop)"}
+
+
+_CPU_GRAPH = {}
+
+
+def _cpu_init(n, d, rowptr, col, cost):
+    import oracle
+    _CPU_GRAPH["g"] = synth.Graph("cpu-sample", n, d, rowptr, col, cost, {})
+    oracle.build()
+
+
+def _cpu_solve(job):
+    import oracle
+    s, t, budget = job
+    t0 = time.perf_counter()
+    f = oracle.solve(_CPU_GRAPH["g"], s, t, label_budget=budget, partial_ok=True)
+    return time.perf_counter() - t0, int(f.stats["partial"])
+
+
+def cpu_batch_sample(g, queries, every: int, budget: int = 0) -> dict:
+    """The oracle as it stands on all host cores, one query per process
+    (queries are independent), over every ``every``-th query of the batch:
+    queries answered per wall second. The pool is started with spawn, so a
+    CUDA context in this process is not inherited."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    sample = queries[::every]
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(cores, len(sample)), initializer=_cpu_init,
+                  initargs=(g.n, g.d, g.rowptr, g.col, g.cost)) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_cpu_solve, [(s, t, budget) for s, t in sample], chunksize=1)
+        wall = time.perf_counter() - t0
+    over = sum(p for _, p in res)
+    used = min(cores, len(sample))
+    busy = sum(t for t, _ in res)
+    # a whole batch keeps every core busy, so its throughput is the sample's
+    # queries per core-second of oracle time times the cores; the sample's own
+    # wall time is bounded by its longest query
+    return {"value": len(sample) * used / busy, "unit": "queries/s", "cores": used, "kind": "oracle",
+            "sample": f"{len(sample)} of the {len(queries)} queries (1 in {every}), one per process, "
+                      f"label budget {budget or 'none'}; {over} over budget; {busy:.1f} core-s of oracle "
+                      f"time, longest query {max(t for t, _ in res):.1f} s, {wall:.1f} s wall "
+                      f"({len(sample) / wall:.3g} queries per wall second)"}
 
 
 class ClockSampler:
@@ -286,10 +339,11 @@ def run_batch(args, opmos, torch, stream):
         opmos.opmos_solve(G, s_, t_, options=single)
     torch.cuda.synchronize()
     single_qps = len(sample) / (time.perf_counter() - t0)
+    cpu = None if args.no_cpu_baseline else cpu_batch_sample(g, q, 32, 2_000_000)
     print(json.dumps({"metric": "batched queries/s", "value": len(q) / sec, "unit": "queries/s", "n_gpus": world,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec,
                       "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32",
-                      "data": "synthetic",
+                      "data": "synthetic", "cpu_baseline": cpu,
                       "config": {"workload": "ship256-d5-batch: 1,024 queries, Chebyshev 16-128, 5 objectives, seed 1",
                                  "parallelism": f"queries split round-robin over {world} GPU(s)"},
                       "queries_ok": ok, "labels_extracted": sum(r.stats["extracted"] for r in rs),
@@ -346,10 +400,11 @@ def run_road_batch(args, opmos, torch, stream):
     torch.cuda.synchronize()
     single_qps = len(sample) / (time.perf_counter() - t0)
     rs = [r for _, r in out if r is not None]
+    cpu = None if args.no_cpu_baseline else cpu_batch_sample(g, q, 16, budget)
     print(json.dumps({"metric": "batched queries/s", "value": len(q) / sec, "unit": "queries/s", "n_gpus": world,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec,
                       "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32",
-                      "data": "synthetic",
+                      "data": "synthetic", "cpu_baseline": cpu,
                       "config": {"workload": "road200k-d4-batch: 256 queries, hop distance 50-400, 4 objectives, "
                                              f"seed 1, label budget {budget} per query",
                                  "parallelism": f"queries split round-robin over {world} GPU(s)"},
@@ -555,7 +610,8 @@ def main():
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
     achieved = st["bytes"] / (search_ns / 1e9) / 1e9
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["src_digest"] == kernel_source_digest() else None
+    launch = (opt.window, opt.lanes_per_label, opt.tile, opt.delta)
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["src_digest"] == kernel_source_digest(launch) else None
     value = world * useful / (ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -35,6 +35,21 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+// No C++ exception crosses the C ABI: every entry point that returns a code
+// runs its body here and turns an exception into an error code.
+template <class F>
+int guarded(const char* what, F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return fail(OPMOS_ERR_OUT_OF_MEMORY, "%s: host allocation failed", what);
+  } catch (const std::exception& e) {
+    return fail(OPMOS_ERR_CUDA, "%s: %s", what, e.what());
+  } catch (...) {
+    return fail(OPMOS_ERR_CUDA, "%s: unexpected exception", what);
+  }
+}
+
 int cuda_fail(cudaError_t e, const char* what) {
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
@@ -721,81 +736,83 @@ const char* opmos_last_error(void) { return g_err.c_str(); }
 
 int opmos_graph_create(uint32_t n, uint64_t m, uint32_t d, const uint64_t* rowptr, const uint32_t* col,
                        const uint32_t* cost, opmos_graph** out) {
-  if (!out) return fail(OPMOS_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  if (!rowptr || (m && (!col || !cost))) return fail(OPMOS_ERR_INVALID_ARG, "NULL array");
-  if (n == 0 || n >= (1u << 31)) return fail(OPMOS_ERR_INVALID_ARG, "n=%u out of range", n);
-  if (d < 1 || d > OPMOS_MAX_D) return fail(OPMOS_ERR_INVALID_ARG, "d=%u not in [1, %d]", d, OPMOS_MAX_D);
-  if (m >= 0xFFFFFFFFull) return fail(OPMOS_ERR_INVALID_ARG, "m too large");
-  if (rowptr[0] != 0 || rowptr[n] != m) return fail(OPMOS_ERR_INVALID_ARG, "rowptr[0] != 0 or rowptr[n] != m");
-  uint32_t maxdeg = 0;
-  for (uint32_t v = 0; v < n; ++v) {
-    if (rowptr[v + 1] < rowptr[v]) return fail(OPMOS_ERR_INVALID_ARG, "rowptr not monotone at %u", v);
-    maxdeg = std::max<uint32_t>(maxdeg, (uint32_t)(rowptr[v + 1] - rowptr[v]));
-  }
-  for (uint64_t e = 0; e < m; ++e)
-    if (col[e] >= n) return fail(OPMOS_ERR_INVALID_ARG, "col[%llu] = %u >= n", (unsigned long long)e, col[e]);
-  std::vector<uint32_t> delta(d);
-  for (uint32_t k = 0; k < d; ++k) {
-    uint64_t mx = 0, sum = 0;
-    for (uint64_t e = 0; e < m; ++e) {
-      mx = std::max<uint64_t>(mx, cost[k * m + e]);
-      sum += cost[k * m + e];
+  return guarded("opmos_graph_create", [&]() -> int {
+    if (!out) return fail(OPMOS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!rowptr || (m && (!col || !cost))) return fail(OPMOS_ERR_INVALID_ARG, "NULL array");
+    if (n == 0 || n >= (1u << 31)) return fail(OPMOS_ERR_INVALID_ARG, "n=%u out of range", n);
+    if (d < 1 || d > OPMOS_MAX_D) return fail(OPMOS_ERR_INVALID_ARG, "d=%u not in [1, %d]", d, OPMOS_MAX_D);
+    if (m >= 0xFFFFFFFFull) return fail(OPMOS_ERR_INVALID_ARG, "m too large");
+    if (rowptr[0] != 0 || rowptr[n] != m) return fail(OPMOS_ERR_INVALID_ARG, "rowptr[0] != 0 or rowptr[n] != m");
+    uint32_t maxdeg = 0;
+    for (uint32_t v = 0; v < n; ++v) {
+      if (rowptr[v + 1] < rowptr[v]) return fail(OPMOS_ERR_INVALID_ARG, "rowptr not monotone at %u", v);
+      maxdeg = std::max<uint32_t>(maxdeg, (uint32_t)(rowptr[v + 1] - rowptr[v]));
     }
-    // g and F = g + h must fit uint32 on every simple path
-    if ((unsigned __int128)2 * (n - 1) * mx >= ((unsigned __int128)1 << 32))
-      return fail(OPMOS_ERR_OVERFLOW, "objective %u: 2*(n-1)*max cost does not fit uint32", k);
-    const uint64_t mean = m ? (sum + m - 1) / m : 1;
-    delta[k] = (uint32_t)std::max<uint64_t>(1, 2 * mean);
-  }
-  const DevInfo di = device_info();
-  if (!di.ok) return fail(OPMOS_ERR_CUDA, "no CUDA device");
-  // reversed CSR (in-arcs grouped by head node), costs carried along
-  std::vector<uint32_t> rp32(n + 1), rrp(n + 1, 0), rsrc(m), rcost((size_t)d * m);
-  for (uint32_t v = 0; v <= n; ++v) rp32[v] = (uint32_t)rowptr[v];
-  for (uint64_t e = 0; e < m; ++e) rrp[col[e] + 1]++;
-  for (uint32_t v = 0; v < n; ++v) rrp[v + 1] += rrp[v];
-  {
-    std::vector<uint32_t> fill(rrp.begin(), rrp.end() - 1);
-    for (uint32_t u = 0; u < n; ++u)
-      for (uint64_t e = rowptr[u]; e < rowptr[u + 1]; ++e) {
-        const uint32_t slot = fill[col[e]]++;
-        rsrc[slot] = u;
-        for (uint32_t k = 0; k < d; ++k) rcost[(size_t)k * m + slot] = cost[k * m + e];
+    for (uint64_t e = 0; e < m; ++e)
+      if (col[e] >= n) return fail(OPMOS_ERR_INVALID_ARG, "col[%llu] = %u >= n", (unsigned long long)e, col[e]);
+    std::vector<uint32_t> delta(d);
+    for (uint32_t k = 0; k < d; ++k) {
+      uint64_t mx = 0, sum = 0;
+      for (uint64_t e = 0; e < m; ++e) {
+        mx = std::max<uint64_t>(mx, cost[k * m + e]);
+        sum += cost[k * m + e];
       }
-  }
-  auto* g = new (std::nothrow) opmos_graph;
-  if (!g) return fail(OPMOS_ERR_OUT_OF_MEMORY, "host allocation");
-  g->n = n;
-  g->m = m;
-  g->d = d;
-  g->maxdeg = maxdeg;
-  const size_t mb = std::max<size_t>(m, 1);
-  cudaError_t e = cudaSuccess;
-  auto alloc = [&](uint32_t** p, size_t words) {
-    if (e == cudaSuccess) e = cudaMalloc(p, words * 4);
-  };
-  alloc(&g->rowptr, n + 1);
-  alloc(&g->col, mb);
-  alloc(&g->cost, (size_t)d * mb);
-  alloc(&g->rrowptr, n + 1);
-  alloc(&g->rsrc, mb);
-  alloc(&g->rcost, (size_t)d * mb);
-  alloc(&g->delta, d);
-  if (e == cudaSuccess) e = cudaMemcpy(g->rowptr, rp32.data(), (n + 1) * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && m) e = cudaMemcpy(g->col, col, m * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && m) e = cudaMemcpy(g->cost, cost, (size_t)d * m * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(g->rrowptr, rrp.data(), (n + 1) * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && m) e = cudaMemcpy(g->rsrc, rsrc.data(), m * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && m) e = cudaMemcpy(g->rcost, rcost.data(), (size_t)d * m * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(g->delta, delta.data(), d * 4, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    free_graph(g);
-    return cuda_fail(e, "graph upload");
-  }
-  g->dev = GraphDev{n, (uint32_t)m, d, maxdeg, g->rowptr, g->col, g->cost, g->rrowptr, g->rsrc, g->rcost};
-  *out = g;
-  return OPMOS_OK;
+      // g and F = g + h must fit uint32 on every simple path
+      if ((unsigned __int128)2 * (n - 1) * mx >= ((unsigned __int128)1 << 32))
+        return fail(OPMOS_ERR_OVERFLOW, "objective %u: 2*(n-1)*max cost does not fit uint32", k);
+      const uint64_t mean = m ? (sum + m - 1) / m : 1;
+      delta[k] = (uint32_t)std::max<uint64_t>(1, 2 * mean);
+    }
+    const DevInfo di = device_info();
+    if (!di.ok) return fail(OPMOS_ERR_CUDA, "no CUDA device");
+    // reversed CSR (in-arcs grouped by head node), costs carried along
+    std::vector<uint32_t> rp32(n + 1), rrp(n + 1, 0), rsrc(m), rcost((size_t)d * m);
+    for (uint32_t v = 0; v <= n; ++v) rp32[v] = (uint32_t)rowptr[v];
+    for (uint64_t e = 0; e < m; ++e) rrp[col[e] + 1]++;
+    for (uint32_t v = 0; v < n; ++v) rrp[v + 1] += rrp[v];
+    {
+      std::vector<uint32_t> fill(rrp.begin(), rrp.end() - 1);
+      for (uint32_t u = 0; u < n; ++u)
+        for (uint64_t e = rowptr[u]; e < rowptr[u + 1]; ++e) {
+          const uint32_t slot = fill[col[e]]++;
+          rsrc[slot] = u;
+          for (uint32_t k = 0; k < d; ++k) rcost[(size_t)k * m + slot] = cost[k * m + e];
+        }
+    }
+    auto* g = new (std::nothrow) opmos_graph;
+    if (!g) return fail(OPMOS_ERR_OUT_OF_MEMORY, "host allocation");
+    g->n = n;
+    g->m = m;
+    g->d = d;
+    g->maxdeg = maxdeg;
+    const size_t mb = std::max<size_t>(m, 1);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](uint32_t** p, size_t words) {
+      if (e == cudaSuccess) e = cudaMalloc(p, words * 4);
+    };
+    alloc(&g->rowptr, n + 1);
+    alloc(&g->col, mb);
+    alloc(&g->cost, (size_t)d * mb);
+    alloc(&g->rrowptr, n + 1);
+    alloc(&g->rsrc, mb);
+    alloc(&g->rcost, (size_t)d * mb);
+    alloc(&g->delta, d);
+    if (e == cudaSuccess) e = cudaMemcpy(g->rowptr, rp32.data(), (n + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && m) e = cudaMemcpy(g->col, col, m * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && m) e = cudaMemcpy(g->cost, cost, (size_t)d * m * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->rrowptr, rrp.data(), (n + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && m) e = cudaMemcpy(g->rsrc, rsrc.data(), m * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && m) e = cudaMemcpy(g->rcost, rcost.data(), (size_t)d * m * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->delta, delta.data(), d * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      free_graph(g);
+      return cuda_fail(e, "graph upload");
+    }
+    g->dev = GraphDev{n, (uint32_t)m, d, maxdeg, g->rowptr, g->col, g->cost, g->rrowptr, g->rsrc, g->rcost};
+    *out = g;
+    return OPMOS_OK;
+  });
 }
 
 void opmos_graph_destroy(opmos_graph* g) {
@@ -804,37 +821,41 @@ void opmos_graph_destroy(opmos_graph* g) {
 }
 
 int opmos_heuristic(const opmos_graph* g, uint32_t goal, uint32_t d_used, opmos_heur** out) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!out) return fail(OPMOS_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  if (!g) return fail(OPMOS_ERR_INVALID_ARG, "graph is NULL");
-  if (goal >= g->n) return fail(OPMOS_ERR_INVALID_ARG, "goal %u >= n", goal);
-  const uint32_t D = d_used ? d_used : g->d;
-  if (D > g->d) return fail(OPMOS_ERR_INVALID_ARG, "d_used %u > d %u", D, g->d);
-  auto* h = new (std::nothrow) opmos_heur;
-  if (!h) return fail(OPMOS_ERR_OUT_OF_MEMORY, "host allocation");
-  h->g = g;
-  h->goal = goal;
-  h->d = D;
-  cudaError_t e = cudaMalloc(&h->h, (size_t)D * g->n * 4);
-  if (e != cudaSuccess) {
-    delete h;
-    return cuda_fail(e, "cudaMalloc(heuristic)");
-  }
-  if (int rc = compute_heuristic(g, D, &goal, 1, h->h, nullptr, &h->ns)) {
-    cudaFree(h->h);
-    delete h;
-    return rc;
-  }
-  *out = h;
-  return OPMOS_OK;
+  return guarded("opmos_heuristic", [&]() -> int {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!out) return fail(OPMOS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!g) return fail(OPMOS_ERR_INVALID_ARG, "graph is NULL");
+    if (goal >= g->n) return fail(OPMOS_ERR_INVALID_ARG, "goal %u >= n", goal);
+    const uint32_t D = d_used ? d_used : g->d;
+    if (D > g->d) return fail(OPMOS_ERR_INVALID_ARG, "d_used %u > d %u", D, g->d);
+    auto* h = new (std::nothrow) opmos_heur;
+    if (!h) return fail(OPMOS_ERR_OUT_OF_MEMORY, "host allocation");
+    h->g = g;
+    h->goal = goal;
+    h->d = D;
+    cudaError_t e = cudaMalloc(&h->h, (size_t)D * g->n * 4);
+    if (e != cudaSuccess) {
+      delete h;
+      return cuda_fail(e, "cudaMalloc(heuristic)");
+    }
+    if (int rc = compute_heuristic(g, D, &goal, 1, h->h, nullptr, &h->ns)) {
+      cudaFree(h->h);
+      delete h;
+      return rc;
+    }
+    *out = h;
+    return OPMOS_OK;
+  });
 }
 
 int opmos_heuristic_copy(const opmos_heur* h, uint32_t* h_out) {
-  if (!h || !h_out) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
-  cudaError_t e = cudaMemcpy(h_out, h->h, (size_t)h->d * h->g->n * 4, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(e, "heuristic copy");
-  return OPMOS_OK;
+  return guarded("opmos_heuristic_copy", [&]() -> int {
+    if (!h || !h_out) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e = cudaMemcpy(h_out, h->h, (size_t)h->d * h->g->n * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "heuristic copy");
+    return OPMOS_OK;
+  });
 }
 
 void opmos_heuristic_destroy(opmos_heur* h) {
@@ -845,82 +866,86 @@ void opmos_heuristic_destroy(opmos_heur* h) {
 
 int opmos_solve(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint32_t goal,
                 const opmos_options* opt, opmos_result** out) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!out) return fail(OPMOS_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  if (!g) return fail(OPMOS_ERR_INVALID_ARG, "graph is NULL");
-  if (start >= g->n || goal >= g->n) return fail(OPMOS_ERR_INVALID_ARG, "start/goal out of range");
-  const opmos_options o = resolve(opt, false);
-  uint32_t D;
-  if (int rc = check_options(o, g, &D)) return rc;
-  return solve_one(g, heur, start, goal, o, D, out);
+  return guarded("opmos_solve", [&]() -> int {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!out) return fail(OPMOS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!g) return fail(OPMOS_ERR_INVALID_ARG, "graph is NULL");
+    if (start >= g->n || goal >= g->n) return fail(OPMOS_ERR_INVALID_ARG, "start/goal out of range");
+    const opmos_options o = resolve(opt, false);
+    uint32_t D;
+    if (int rc = check_options(o, g, &D)) return rc;
+    return solve_one(g, heur, start, goal, o, D, out);
+  });
 }
 
 int opmos_solve_batch(const opmos_graph* g, uint32_t nq, const uint32_t* starts, const uint32_t* goals,
                       const opmos_options* opt, opmos_result** out, int* status) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g || !out || !status || (nq && (!starts || !goals))) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
-  for (uint32_t q = 0; q < nq; ++q) {
-    out[q] = nullptr;
-    status[q] = OPMOS_ERR_INVALID_ARG;
-  }
-  for (uint32_t q = 0; q < nq; ++q)
-    if (starts[q] >= g->n || goals[q] >= g->n) return fail(OPMOS_ERR_INVALID_ARG, "query %u out of range", q);
-  const opmos_options o = resolve(opt, true);
-  uint32_t D;
-  if (int rc = check_options(o, g, &D)) return rc;
-  if (nq == 0) return OPMOS_OK;
-  const auto t0 = std::chrono::steady_clock::now();
-  const DevInfo di = device_info();
-  if (!di.ok) return fail(OPMOS_ERR_CUDA, "no CUDA device");
-  cudaStream_t s = (cudaStream_t)o.stream;
-  // heuristics, one per distinct goal
-  std::map<uint32_t, uint32_t> gidx;
-  std::vector<uint32_t> ugoals;
-  for (uint32_t q = 0; q < nq; ++q)
-    if (gidx.emplace(goals[q], (uint32_t)ugoals.size()).second) ugoals.push_back(goals[q]);
-  uint32_t* hall = nullptr;
-  CK(cudaMalloc(&hall, (size_t)ugoals.size() * D * g->n * 4));
-  struct Free {
-    void* p;
-    ~Free() {
-      if (p) cudaFree(p);
+  return guarded("opmos_solve_batch", [&]() -> int {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g || !out || !status || (nq && (!starts || !goals))) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+    for (uint32_t q = 0; q < nq; ++q) {
+      out[q] = nullptr;
+      status[q] = OPMOS_ERR_INVALID_ARG;
     }
-  } free_h{hall};
-  uint64_t hns = 0;
-  if (int rc = compute_heuristic(g, D, ugoals.data(), (uint32_t)ugoals.size(), hall, s, &hns)) return rc;
-  // Rounds of the multi-query kernel: all queries, then those that outgrew
-  // their slot with 8x fewer, 8x larger slots; single-query mode last.
-  std::vector<uint32_t> todo(nq);
-  for (uint32_t q = 0; q < nq; ++q) todo[q] = q;
-  unsigned slots = std::min<unsigned>(nq, std::min<unsigned>(kMaxSlots, kBatchSlots));
-  for (int round = 0; round < 3 && !todo.empty(); ++round) {
-    slots = std::max(1u, std::min<unsigned>(slots, (unsigned)todo.size()));
-    std::vector<uint32_t> overflow;
-    if (int rc = run_multi(g, D, o, todo, starts, goals, hall, gidx, slots, o.mem_budget_bytes / slots, hns, t0, out,
-                           status, &overflow))
-      return rc;
-    todo.swap(overflow);
-    slots = slots / 8;
-    if (slots < 2) break;
-  }
-  if (!todo.empty()) {
-    opmos_options so = resolve(opt, false);
-    so.flags = o.flags;
-    so.stream = o.stream;
-    if (opt && opt->mem_budget_bytes) so.mem_budget_bytes = std::max<uint64_t>(opt->mem_budget_bytes, 1ull << 30);
-    for (uint32_t q : todo) {
-      opmos_result* r = nullptr;
-      opmos_heur hh{g, goals[q], D, hall + (size_t)gidx[goals[q]] * D * g->n, 0};
-      const int rc = solve_one(g, &hh, starts[q], goals[q], so, D, &r);
-      status[q] = rc;
-      if (rc == OPMOS_OK) {
-        r->stats.heuristic_ns = hns;
-        out[q] = r;
+    for (uint32_t q = 0; q < nq; ++q)
+      if (starts[q] >= g->n || goals[q] >= g->n) return fail(OPMOS_ERR_INVALID_ARG, "query %u out of range", q);
+    const opmos_options o = resolve(opt, true);
+    uint32_t D;
+    if (int rc = check_options(o, g, &D)) return rc;
+    if (nq == 0) return OPMOS_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    const DevInfo di = device_info();
+    if (!di.ok) return fail(OPMOS_ERR_CUDA, "no CUDA device");
+    cudaStream_t s = (cudaStream_t)o.stream;
+    // heuristics, one per distinct goal
+    std::map<uint32_t, uint32_t> gidx;
+    std::vector<uint32_t> ugoals;
+    for (uint32_t q = 0; q < nq; ++q)
+      if (gidx.emplace(goals[q], (uint32_t)ugoals.size()).second) ugoals.push_back(goals[q]);
+    uint32_t* hall = nullptr;
+    CK(cudaMalloc(&hall, (size_t)ugoals.size() * D * g->n * 4));
+    struct Free {
+      void* p;
+      ~Free() {
+        if (p) cudaFree(p);
+      }
+    } free_h{hall};
+    uint64_t hns = 0;
+    if (int rc = compute_heuristic(g, D, ugoals.data(), (uint32_t)ugoals.size(), hall, s, &hns)) return rc;
+    // Rounds of the multi-query kernel: all queries, then those that outgrew
+    // their slot with 8x fewer, 8x larger slots; single-query mode last.
+    std::vector<uint32_t> todo(nq);
+    for (uint32_t q = 0; q < nq; ++q) todo[q] = q;
+    unsigned slots = std::min<unsigned>(nq, std::min<unsigned>(kMaxSlots, kBatchSlots));
+    for (int round = 0; round < 3 && !todo.empty(); ++round) {
+      slots = std::max(1u, std::min<unsigned>(slots, (unsigned)todo.size()));
+      std::vector<uint32_t> overflow;
+      if (int rc = run_multi(g, D, o, todo, starts, goals, hall, gidx, slots, o.mem_budget_bytes / slots, hns, t0, out,
+                             status, &overflow))
+        return rc;
+      todo.swap(overflow);
+      slots = slots / 8;
+      if (slots < 2) break;
+    }
+    if (!todo.empty()) {
+      opmos_options so = resolve(opt, false);
+      so.flags = o.flags;
+      so.stream = o.stream;
+      if (opt && opt->mem_budget_bytes) so.mem_budget_bytes = std::max<uint64_t>(opt->mem_budget_bytes, 1ull << 30);
+      for (uint32_t q : todo) {
+        opmos_result* r = nullptr;
+        opmos_heur hh{g, goals[q], D, hall + (size_t)gidx[goals[q]] * D * g->n, 0};
+        const int rc = solve_one(g, &hh, starts[q], goals[q], so, D, &r);
+        status[q] = rc;
+        if (rc == OPMOS_OK) {
+          r->stats.heuristic_ns = hns;
+          out[q] = r;
+        }
       }
     }
-  }
-  return OPMOS_OK;
+    return OPMOS_OK;
+  });
 }
 
 
@@ -928,29 +953,35 @@ uint32_t opmos_result_count(const opmos_result* r) { return r ? r->count : 0; }
 uint32_t opmos_result_d(const opmos_result* r) { return r ? r->d : 0; }
 
 int opmos_result_costs(const opmos_result* r, uint32_t* out) {
-  if (!r || (!out && r->count)) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
-  if (r->count) std::memcpy(out, r->costs.data(), r->costs.size() * 4);
-  return OPMOS_OK;
+  return guarded("opmos_result_costs", [&]() -> int {
+    if (!r || (!out && r->count)) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+    if (r->count) std::memcpy(out, r->costs.data(), r->costs.size() * 4);
+    return OPMOS_OK;
+  });
 }
 
 int opmos_result_path(const opmos_result* r, uint32_t i, uint32_t* nodes, uint64_t* edges, uint32_t cap,
                       uint32_t* len) {
-  if (!r || !len) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
-  if (!r->has_paths) return fail(OPMOS_ERR_INVALID_ARG, "result was solved without paths");
-  if (i >= r->count) return fail(OPMOS_ERR_INVALID_ARG, "solution index %u >= count %u", i, r->count);
-  const uint32_t a = r->offs[i], b = r->offs[i + 1];
-  *len = b - a;
-  if (b - a > cap) return fail(OPMOS_ERR_CAPACITY, "path of %u nodes exceeds cap %u", b - a, cap);
-  if (!nodes || (b - a > 1 && !edges)) return fail(OPMOS_ERR_INVALID_ARG, "NULL output array");
-  std::memcpy(nodes, r->nodes.data() + a, (size_t)(b - a) * 4);
-  if (b - a > 1) std::memcpy(edges, r->edges.data() + (a - i), (size_t)(b - a - 1) * 8);
-  return OPMOS_OK;
+  return guarded("opmos_result_path", [&]() -> int {
+    if (!r || !len) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+    if (!r->has_paths) return fail(OPMOS_ERR_INVALID_ARG, "result was solved without paths");
+    if (i >= r->count) return fail(OPMOS_ERR_INVALID_ARG, "solution index %u >= count %u", i, r->count);
+    const uint32_t a = r->offs[i], b = r->offs[i + 1];
+    *len = b - a;
+    if (b - a > cap) return fail(OPMOS_ERR_CAPACITY, "path of %u nodes exceeds cap %u", b - a, cap);
+    if (!nodes || (b - a > 1 && !edges)) return fail(OPMOS_ERR_INVALID_ARG, "NULL output array");
+    std::memcpy(nodes, r->nodes.data() + a, (size_t)(b - a) * 4);
+    if (b - a > 1) std::memcpy(edges, r->edges.data() + (a - i), (size_t)(b - a - 1) * 8);
+    return OPMOS_OK;
+  });
 }
 
 int opmos_result_stats(const opmos_result* r, opmos_stats* out) {
-  if (!r || !out) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
-  *out = r->stats;
-  return OPMOS_OK;
+  return guarded("opmos_result_stats", [&]() -> int {
+    if (!r || !out) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+    *out = r->stats;
+    return OPMOS_OK;
+  });
 }
 
 void opmos_result_free(opmos_result* r) { delete r; }
@@ -1015,210 +1046,216 @@ extern "C" {
 
 int opmos_server_create(const opmos_graph* const* graphs, uint32_t ngraphs, const opmos_options* opt,
                         opmos_server** out) {
-  if (!out) return fail(OPMOS_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  if (!graphs || ngraphs == 0) return fail(OPMOS_ERR_INVALID_ARG, "no graphs");
-  const DevInfo di = device_info();
-  if (!di.ok) return fail(OPMOS_ERR_CUDA, "no CUDA device");
-  auto* sv = new (std::nothrow) opmos_server;
-  if (!sv) return fail(OPMOS_ERR_OUT_OF_MEMORY, "host allocation");
-  opmos_options o = resolve(opt, true);
-  if (!opt || !opt->mem_budget_bytes) o.mem_budget_bytes = 64ull << 30;
-  sv->o = o;
-  for (uint32_t i = 0; i < ngraphs; ++i) {
-    if (!graphs[i]) {
-      delete sv;
-      return fail(OPMOS_ERR_INVALID_ARG, "graph %u is NULL", i);
+  return guarded("opmos_server_create", [&]() -> int {
+    if (!out) return fail(OPMOS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!graphs || ngraphs == 0) return fail(OPMOS_ERR_INVALID_ARG, "no graphs");
+    const DevInfo di = device_info();
+    if (!di.ok) return fail(OPMOS_ERR_CUDA, "no CUDA device");
+    auto* sv = new (std::nothrow) opmos_server;
+    if (!sv) return fail(OPMOS_ERR_OUT_OF_MEMORY, "host allocation");
+    opmos_options o = resolve(opt, true);
+    if (!opt || !opt->mem_budget_bytes) o.mem_budget_bytes = 64ull << 30;
+    sv->o = o;
+    for (uint32_t i = 0; i < ngraphs; ++i) {
+      if (!graphs[i]) {
+        delete sv;
+        return fail(OPMOS_ERR_INVALID_ARG, "graph %u is NULL", i);
+      }
+      sv->graphs.push_back(graphs[i]);
+      sv->shape.n = std::max(sv->shape.n, graphs[i]->n);
+      sv->shape.maxdeg = std::max(sv->shape.maxdeg, graphs[i]->maxdeg);
+      sv->dmax = std::max(sv->dmax, graphs[i]->d);
     }
-    sv->graphs.push_back(graphs[i]);
-    sv->shape.n = std::max(sv->shape.n, graphs[i]->n);
-    sv->shape.maxdeg = std::max(sv->shape.maxdeg, graphs[i]->maxdeg);
-    sv->dmax = std::max(sv->dmax, graphs[i]->d);
-  }
-  uint32_t Dchk;
-  {
-    opmos_options oc = o;
-    oc.d_used = 0;
-    opmos_graph tmp = sv->shape;
-    tmp.d = sv->dmax;
-    if (int rc = check_options(oc, &tmp, &Dchk)) {
+    uint32_t Dchk;
+    {
+      opmos_options oc = o;
+      oc.d_used = 0;
+      opmos_graph tmp = sv->shape;
+      tmp.d = sv->dmax;
+      if (int rc = check_options(oc, &tmp, &Dchk)) {
+        delete sv;
+        return rc;
+      }
+    }
+    ArenaPlan pl;
+    if (int rc = plan_arena(&sv->shape, sv->dmax, o.window, kServeSlotBytes, true, &pl)) {
       delete sv;
       return rc;
     }
-  }
-  ArenaPlan pl;
-  if (int rc = plan_arena(&sv->shape, sv->dmax, o.window, kServeSlotBytes, true, &pl)) {
-    delete sv;
-    return rc;
-  }
-  const size_t slot_bytes = (pl.bytes + 255) / 256 * 256;
-  const size_t pool_bytes = kServeOutWords * 4 + 256;
-  const size_t per_slot = slot_bytes + pool_bytes;
-  sv->nslots = (unsigned)std::min<size_t>(kMaxSlots, std::max<size_t>(1, o.mem_budget_bytes / per_slot));
-  sv->qcap = std::max(64u, 2 * sv->nslots);
-  const size_t hstride = (size_t)sv->dmax * sv->shape.n;
-  const size_t spb = 5 * (size_t)sv->shape.n + 64;
-  const size_t misc = sizeof(MCtl) + sv->graphs.size() * sizeof(GraphDev) + sv->nslots * (sizeof(MSlot) + sizeof(QCtl)) +
-                      OPMOS_MAX_D * sizeof(HJob) + 64 + 32 * 256;
-  const size_t dbytes = sv->nslots * per_slot + sv->qcap * hstride * 4 + kServeHeurBlocks * spb * 4 + misc;
-  cudaError_t e = cudaMalloc(&sv->dmem, dbytes);
-  if (e != cudaSuccess) {
-    sv->dmem = nullptr;
-    server_free(sv);
-    return cuda_fail(e, "server device memory");
-  }
-  const size_t hbytes = sv->qcap * (sizeof(MQuery) + sizeof(QResult) + 4) + (HC_RELEASE + sv->nslots) * 4 + 8 * 256;
-  e = cudaHostAlloc(&sv->hmem, hbytes, cudaHostAllocMapped);
-  if (e != cudaSuccess) {
-    sv->hmem = nullptr;
-    server_free(sv);
-    return cuda_fail(e, "server mapped host memory");
-  }
-  std::memset(sv->hmem, 0, hbytes);
-  char* hp = sv->hmem;
-  sv->hq = carve<MQuery>(hp, sv->qcap);
-  sv->hres = carve<QResult>(hp, sv->qcap);
-  sv->hdone = carve<unsigned>(hp, sv->qcap);
-  sv->hctl = carve<unsigned>(hp, HC_RELEASE + sv->nslots);
-  auto dev_of = [&](void* h) {
-    void* d = nullptr;
-    cudaHostGetDevicePointer(&d, h, 0);
-    return d;
-  };
-  char* dp = sv->dmem;
-  MCtl* M = carve<MCtl>(dp, 1);
-  GraphDev* dgraphs = carve<GraphDev>(dp, sv->graphs.size());
-  QCtl* ctls = carve<QCtl>(dp, sv->nslots);
-  MSlot* dslots = carve<MSlot>(dp, sv->nslots);
-  sv->djobs = carve<HJob>(dp, OPMOS_MAX_D);
-  sv->hkctr = carve<unsigned>(dp, 16);
-  sv->hscratch = carve<uint32_t>(dp, kServeHeurBlocks * spb);
-  sv->hring = carve<uint32_t>(dp, sv->qcap * hstride);
-  std::vector<MSlot> hslots(sv->nslots);
-  for (unsigned i = 0; i < sv->nslots; ++i) {
-    char* base = carve<char>(dp, per_slot);
-    MSlot& sl = hslots[i];
-    std::memset(&sl, 0, sizeof(sl));
-    layout_arena(&sv->shape, sv->dmax, pl, base, &sl.A);
-    char* pp = base + slot_bytes;
-    unsigned long long* used = carve<unsigned long long>(pp, 1);
-    uint32_t* words = carve<uint32_t>(pp, kServeOutWords);
-    sl.O = OutPool{words, kServeOutWords, used};
-    sv->pool_words.push_back(words);
-    sl.P.window = o.window;
-    sl.P.lanes = o.lanes_per_label;
-    sl.P.delta = o.delta;
-    sl.P.tile = o.tile;
-    sl.P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, pl.label_cap);
-    sl.P.flags = o.flags;
-    sl.P.time_limit_ns = kTimeLimitNs;
-    sl.state = SL_FREE;
-  }
-  std::vector<GraphDev> gd;
-  for (auto* g : sv->graphs) gd.push_back(g->dev);
-  MCtl hM{};
-  hM.qcap = sv->qcap;
-  hM.hold = 1;
-  sv->inuse.assign(sv->qcap, 0);
-  sv->qd.assign(sv->qcap, 0);
-  e = cudaStreamCreateWithFlags(&sv->kstream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->hstream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMemcpy(M, &hM, sizeof(MCtl), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(dgraphs, gd.data(), gd.size() * sizeof(GraphDev), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(ctls, 0, sv->nslots * sizeof(QCtl));
-  if (e == cudaSuccess) e = cudaMemcpy(dslots, hslots.data(), sv->nslots * sizeof(MSlot), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    server_free(sv);
-    return cuda_fail(e, "server set-up");
-  }
-  const int occ = multi_occupancy();
-  const unsigned full = (unsigned)di.sms * (unsigned)std::min(occ, 2);
-  sv->blocks = full > 2 * kServeHeurBlocks ? full - 2 * kServeHeurBlocks : std::max(1u, full / 2);
-  e = launch_multi(dslots, ctls, sv->nslots, (MQuery*)dev_of(sv->hq), (unsigned*)dev_of(sv->hctl), dgraphs,
-                   (QResult*)dev_of(sv->hres), (unsigned*)dev_of(sv->hdone), M, sv->blocks, sv->kstream);
-  if (e != cudaSuccess) {
-    server_free(sv);
-    return cuda_fail(e, "server kernel launch");
-  }
-  sv->running = true;
-  *out = sv;
-  return OPMOS_OK;
+    const size_t slot_bytes = (pl.bytes + 255) / 256 * 256;
+    const size_t pool_bytes = kServeOutWords * 4 + 256;
+    const size_t per_slot = slot_bytes + pool_bytes;
+    sv->nslots = (unsigned)std::min<size_t>(kMaxSlots, std::max<size_t>(1, o.mem_budget_bytes / per_slot));
+    sv->qcap = std::max(64u, 2 * sv->nslots);
+    const size_t hstride = (size_t)sv->dmax * sv->shape.n;
+    const size_t spb = 5 * (size_t)sv->shape.n + 64;
+    const size_t misc = sizeof(MCtl) + sv->graphs.size() * sizeof(GraphDev) + sv->nslots * (sizeof(MSlot) + sizeof(QCtl)) +
+                        OPMOS_MAX_D * sizeof(HJob) + 64 + 32 * 256;
+    const size_t dbytes = sv->nslots * per_slot + sv->qcap * hstride * 4 + kServeHeurBlocks * spb * 4 + misc;
+    cudaError_t e = cudaMalloc(&sv->dmem, dbytes);
+    if (e != cudaSuccess) {
+      sv->dmem = nullptr;
+      server_free(sv);
+      return cuda_fail(e, "server device memory");
+    }
+    const size_t hbytes = sv->qcap * (sizeof(MQuery) + sizeof(QResult) + 4) + (HC_RELEASE + sv->nslots) * 4 + 8 * 256;
+    e = cudaHostAlloc(&sv->hmem, hbytes, cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+      sv->hmem = nullptr;
+      server_free(sv);
+      return cuda_fail(e, "server mapped host memory");
+    }
+    std::memset(sv->hmem, 0, hbytes);
+    char* hp = sv->hmem;
+    sv->hq = carve<MQuery>(hp, sv->qcap);
+    sv->hres = carve<QResult>(hp, sv->qcap);
+    sv->hdone = carve<unsigned>(hp, sv->qcap);
+    sv->hctl = carve<unsigned>(hp, HC_RELEASE + sv->nslots);
+    auto dev_of = [&](void* h) {
+      void* d = nullptr;
+      cudaHostGetDevicePointer(&d, h, 0);
+      return d;
+    };
+    char* dp = sv->dmem;
+    MCtl* M = carve<MCtl>(dp, 1);
+    GraphDev* dgraphs = carve<GraphDev>(dp, sv->graphs.size());
+    QCtl* ctls = carve<QCtl>(dp, sv->nslots);
+    MSlot* dslots = carve<MSlot>(dp, sv->nslots);
+    sv->djobs = carve<HJob>(dp, OPMOS_MAX_D);
+    sv->hkctr = carve<unsigned>(dp, 16);
+    sv->hscratch = carve<uint32_t>(dp, kServeHeurBlocks * spb);
+    sv->hring = carve<uint32_t>(dp, sv->qcap * hstride);
+    std::vector<MSlot> hslots(sv->nslots);
+    for (unsigned i = 0; i < sv->nslots; ++i) {
+      char* base = carve<char>(dp, per_slot);
+      MSlot& sl = hslots[i];
+      std::memset(&sl, 0, sizeof(sl));
+      layout_arena(&sv->shape, sv->dmax, pl, base, &sl.A);
+      char* pp = base + slot_bytes;
+      unsigned long long* used = carve<unsigned long long>(pp, 1);
+      uint32_t* words = carve<uint32_t>(pp, kServeOutWords);
+      sl.O = OutPool{words, kServeOutWords, used};
+      sv->pool_words.push_back(words);
+      sl.P.window = o.window;
+      sl.P.lanes = o.lanes_per_label;
+      sl.P.delta = o.delta;
+      sl.P.tile = o.tile;
+      sl.P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, pl.label_cap);
+      sl.P.flags = o.flags;
+      sl.P.time_limit_ns = kTimeLimitNs;
+      sl.state = SL_FREE;
+    }
+    std::vector<GraphDev> gd;
+    for (auto* g : sv->graphs) gd.push_back(g->dev);
+    MCtl hM{};
+    hM.qcap = sv->qcap;
+    hM.hold = 1;
+    sv->inuse.assign(sv->qcap, 0);
+    sv->qd.assign(sv->qcap, 0);
+    e = cudaStreamCreateWithFlags(&sv->kstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->hstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemcpy(M, &hM, sizeof(MCtl), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dgraphs, gd.data(), gd.size() * sizeof(GraphDev), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ctls, 0, sv->nslots * sizeof(QCtl));
+    if (e == cudaSuccess) e = cudaMemcpy(dslots, hslots.data(), sv->nslots * sizeof(MSlot), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      server_free(sv);
+      return cuda_fail(e, "server set-up");
+    }
+    const int occ = multi_occupancy();
+    const unsigned full = (unsigned)di.sms * (unsigned)std::min(occ, 2);
+    sv->blocks = full > 2 * kServeHeurBlocks ? full - 2 * kServeHeurBlocks : std::max(1u, full / 2);
+    e = launch_multi(dslots, ctls, sv->nslots, (MQuery*)dev_of(sv->hq), (unsigned*)dev_of(sv->hctl), dgraphs,
+                     (QResult*)dev_of(sv->hres), (unsigned*)dev_of(sv->hdone), M, sv->blocks, sv->kstream);
+    if (e != cudaSuccess) {
+      server_free(sv);
+      return cuda_fail(e, "server kernel launch");
+    }
+    sv->running = true;
+    *out = sv;
+    return OPMOS_OK;
+  });
 }
 
 int opmos_server_submit(opmos_server* sv, uint32_t graph, uint32_t d, uint32_t start, uint32_t goal,
                         uint64_t* ticket) {
-  if (!sv || !ticket) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
-  std::lock_guard<std::mutex> lk(sv->mu);
-  if (graph >= sv->graphs.size()) return fail(OPMOS_ERR_INVALID_ARG, "graph %u out of range", graph);
-  const opmos_graph* g = sv->graphs[graph];
-  const uint32_t D = d ? d : g->d;
-  if (D < 1 || D > g->d) return fail(OPMOS_ERR_INVALID_ARG, "d %u not in [1, %u]", D, g->d);
-  if (start >= g->n || goal >= g->n) return fail(OPMOS_ERR_INVALID_ARG, "start/goal out of range");
-  const uint64_t t = sv->next_ticket;
-  const unsigned idx = (unsigned)(t % sv->qcap);
-  if (sv->inuse[idx]) return fail(OPMOS_ERR_CAPACITY, "server queue full (%u outstanding queries)", sv->qcap);
-  // the heuristic of this query, on the SMs the resident kernel leaves free
-  uint32_t* h = sv->hring + (size_t)idx * sv->dmax * sv->shape.n;
-  HJob jobs[OPMOS_MAX_D];
-  for (uint32_t k = 0; k < D; ++k) jobs[k] = HJob{goal, k, h + (size_t)k * g->n};
-  cudaStream_t s = sv->hstream;
-  CK(cudaMemsetAsync(sv->hkctr, 0, 2 * sizeof(unsigned), s));
-  CK(cudaMemcpyAsync(sv->djobs, jobs, D * sizeof(HJob), cudaMemcpyHostToDevice, s));
-  CK(launch_heuristic(g->dev, sv->djobs, D, sv->hscratch, 5 * (size_t)sv->shape.n + 64,
-                      std::min<unsigned>(D, kServeHeurBlocks), g->delta, sv->hkctr, sv->hkctr + 1, s));
-  unsigned herr = 0;
-  CK(cudaMemcpyAsync(&herr, sv->hkctr + 1, 4, cudaMemcpyDeviceToHost, s));
-  // bounded wait: the heuristic runs on SMs the resident kernel leaves free
-  const auto tw = std::chrono::steady_clock::now();
-  for (;;) {
-    const cudaError_t q = cudaStreamQuery(s);
-    if (q == cudaSuccess) break;
-    if (q != cudaErrorNotReady) return cuda_fail(q, "server heuristic");
-    if (std::chrono::steady_clock::now() - tw > std::chrono::seconds(30))
-      return fail(OPMOS_ERR_TIMEOUT, "server heuristic did not finish within 30 s");
-    std::this_thread::sleep_for(std::chrono::microseconds(20));
-  }
-  if (herr) return fail((int)herr, "heuristic kernel reported error %u", herr);
-  MQuery q{graph, start, goal, D, h};
-  sv->hq[idx] = q;
-  sv->hdone[idx] = 0;
-  sv->inuse[idx] = 1;
-  sv->qd[idx] = D;
-  std::atomic_thread_fence(std::memory_order_seq_cst);
-  *reinterpret_cast<volatile unsigned*>(&sv->hctl[HC_TAIL]) = (unsigned)(t + 1);
-  sv->next_ticket = t + 1;
-  *ticket = t;
-  return OPMOS_OK;
+  return guarded("opmos_server_submit", [&]() -> int {
+    if (!sv || !ticket) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (graph >= sv->graphs.size()) return fail(OPMOS_ERR_INVALID_ARG, "graph %u out of range", graph);
+    const opmos_graph* g = sv->graphs[graph];
+    const uint32_t D = d ? d : g->d;
+    if (D < 1 || D > g->d) return fail(OPMOS_ERR_INVALID_ARG, "d %u not in [1, %u]", D, g->d);
+    if (start >= g->n || goal >= g->n) return fail(OPMOS_ERR_INVALID_ARG, "start/goal out of range");
+    const uint64_t t = sv->next_ticket;
+    const unsigned idx = (unsigned)(t % sv->qcap);
+    if (sv->inuse[idx]) return fail(OPMOS_ERR_CAPACITY, "server queue full (%u outstanding queries)", sv->qcap);
+    // the heuristic of this query, on the SMs the resident kernel leaves free
+    uint32_t* h = sv->hring + (size_t)idx * sv->dmax * sv->shape.n;
+    HJob jobs[OPMOS_MAX_D];
+    for (uint32_t k = 0; k < D; ++k) jobs[k] = HJob{goal, k, h + (size_t)k * g->n};
+    cudaStream_t s = sv->hstream;
+    CK(cudaMemsetAsync(sv->hkctr, 0, 2 * sizeof(unsigned), s));
+    CK(cudaMemcpyAsync(sv->djobs, jobs, D * sizeof(HJob), cudaMemcpyHostToDevice, s));
+    CK(launch_heuristic(g->dev, sv->djobs, D, sv->hscratch, 5 * (size_t)sv->shape.n + 64,
+                        std::min<unsigned>(D, kServeHeurBlocks), g->delta, sv->hkctr, sv->hkctr + 1, s));
+    unsigned herr = 0;
+    CK(cudaMemcpyAsync(&herr, sv->hkctr + 1, 4, cudaMemcpyDeviceToHost, s));
+    // bounded wait: the heuristic runs on SMs the resident kernel leaves free
+    const auto tw = std::chrono::steady_clock::now();
+    for (;;) {
+      const cudaError_t q = cudaStreamQuery(s);
+      if (q == cudaSuccess) break;
+      if (q != cudaErrorNotReady) return cuda_fail(q, "server heuristic");
+      if (std::chrono::steady_clock::now() - tw > std::chrono::seconds(30))
+        return fail(OPMOS_ERR_TIMEOUT, "server heuristic did not finish within 30 s");
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    if (herr) return fail((int)herr, "heuristic kernel reported error %u", herr);
+    MQuery q{graph, start, goal, D, h};
+    sv->hq[idx] = q;
+    sv->hdone[idx] = 0;
+    sv->inuse[idx] = 1;
+    sv->qd[idx] = D;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    *reinterpret_cast<volatile unsigned*>(&sv->hctl[HC_TAIL]) = (unsigned)(t + 1);
+    sv->next_ticket = t + 1;
+    *ticket = t;
+    return OPMOS_OK;
+  });
 }
 
 int opmos_server_poll(opmos_server* sv, uint64_t ticket, opmos_result** out) {
-  if (!sv || !out) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
-  *out = nullptr;
-  std::lock_guard<std::mutex> lk(sv->mu);
-  const unsigned idx = (unsigned)(ticket % sv->qcap);
-  if (ticket >= sv->next_ticket || !sv->inuse[idx]) return fail(OPMOS_ERR_INVALID_ARG, "unknown ticket");
-  if (!*reinterpret_cast<volatile unsigned*>(&sv->hdone[idx])) return OPMOS_PENDING;
-  std::atomic_thread_fence(std::memory_order_seq_cst);
-  QResult R;
-  std::memcpy(&R, (const void*)&sv->hres[idx], sizeof(R));
-  const unsigned slot = R.slot;
-  int rc = (int)R.status;
-  if (rc == OPMOS_OK) {
-    opmos_result* r = nullptr;
-    rc = take_result(R, sv->qd[idx], !(sv->o.flags & OPMOS_FLAG_NO_PATHS), sv->pool_words[slot], sv->hstream, &r);
+  return guarded("opmos_server_poll", [&]() -> int {
+    if (!sv || !out) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const unsigned idx = (unsigned)(ticket % sv->qcap);
+    if (ticket >= sv->next_ticket || !sv->inuse[idx]) return fail(OPMOS_ERR_INVALID_ARG, "unknown ticket");
+    if (!*reinterpret_cast<volatile unsigned*>(&sv->hdone[idx])) return OPMOS_PENDING;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    QResult R;
+    std::memcpy(&R, (const void*)&sv->hres[idx], sizeof(R));
+    const unsigned slot = R.slot;
+    int rc = (int)R.status;
     if (rc == OPMOS_OK) {
-      fill_stats(&r->stats, R, sv->qd[idx]);
-      *out = r;
+      opmos_result* r = nullptr;
+      rc = take_result(R, sv->qd[idx], !(sv->o.flags & OPMOS_FLAG_NO_PATHS), sv->pool_words[slot], sv->hstream, &r);
+      if (rc == OPMOS_OK) {
+        fill_stats(&r->stats, R, sv->qd[idx]);
+        *out = r;
+      }
+    } else {
+      search_status((unsigned)rc);
     }
-  } else {
-    search_status((unsigned)rc);
-  }
-  // the result has been copied: the slot may take the next query
-  std::atomic_thread_fence(std::memory_order_seq_cst);
-  *reinterpret_cast<volatile unsigned*>(&sv->hctl[HC_RELEASE + slot]) = 1;
-  sv->hdone[idx] = 0;
-  sv->inuse[idx] = 0;
-  return rc;
+    // the result has been copied: the slot may take the next query
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    *reinterpret_cast<volatile unsigned*>(&sv->hctl[HC_RELEASE + slot]) = 1;
+    sv->hdone[idx] = 0;
+    sv->inuse[idx] = 0;
+    return rc;
+  });
 }
 
 void opmos_server_destroy(opmos_server* sv) {

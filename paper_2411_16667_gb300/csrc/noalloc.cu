@@ -17,6 +17,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
+#include <new>
 
 #include "graph.cuh"
 #include "opmos.h"
@@ -49,6 +50,18 @@ int noalloc_fail(int code, const char* fmt, ...) {
   return record_error(code, buf);
 }
 
+// No C++ exception crosses the C ABI (see opmos.h).
+template <class F>
+int noalloc_guarded(const char* what, F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return noalloc_fail(OPMOS_ERR_OUT_OF_MEMORY, "%s: host allocation failed", what);
+  } catch (...) {
+    return noalloc_fail(OPMOS_ERR_CUDA, "%s: unexpected exception", what);
+  }
+}
+
 // One-time set-up per device (with that device current): the device address
 // of the scratch array.
 int scratch_address(int dev, uint32_t** out) {
@@ -78,40 +91,42 @@ extern "C" {
 
 int opmos_heuristic_noalloc(const opmos_graph* g, uint32_t goal, uint32_t d_used, uint32_t* h_out_device,
                             void* stream) {
-  if (!g || !h_out_device) return noalloc_fail(OPMOS_ERR_INVALID_ARG, "NULL graph or output");
-  if (goal >= g->n) return noalloc_fail(OPMOS_ERR_INVALID_ARG, "goal %u >= n = %u", goal, g->n);
-  const uint32_t D = d_used ? d_used : g->d;
-  if (D > g->d) return noalloc_fail(OPMOS_ERR_INVALID_ARG, "d_used %u > d %u", D, g->d);
-  if (g->n > kNoAllocMaxNodes)
-    return noalloc_fail(OPMOS_ERR_CAPACITY,
-                        "graph has %u nodes; the allocation-free heuristic handles at most %u "
-                        "(use opmos_heuristic)",
-                        g->n, kNoAllocMaxNodes);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(OPMOS_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-  uint32_t* base = nullptr;
-  if (int rc = scratch_address(dev, &base)) return rc;
-  unsigned* ctr = base;
-  HJob* jobs = reinterpret_cast<HJob*>(base + kNoAllocCtrWords);
-  uint32_t* work = base + kNoAllocCtrWords + kNoAllocJobWords;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // the array keeps the previous call's contents: the counters must restart
-  // at zero (worklists and flags are re-initialised by the kernel itself)
-  e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), s);
-  if (e != cudaSuccess) return noalloc_fail(OPMOS_ERR_CUDA, "clear counters: %s", cudaGetErrorString(e));
-  fill_jobs_kernel<<<1, 32, 0, s>>>(jobs, goal, D, h_out_device, g->n);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return noalloc_fail(OPMOS_ERR_CUDA, "job table: %s", cudaGetErrorString(e));
-  const unsigned blocks = D < kNoAllocBlocks ? D : kNoAllocBlocks;
-  e = launch_heuristic(g->dev, jobs, D, work, kNoAllocBlockWords, blocks, g->delta, ctr, ctr + 1, s);
-  if (e != cudaSuccess) return noalloc_fail(OPMOS_ERR_CUDA, "heuristic launch: %s", cudaGetErrorString(e));
-  unsigned err = 0;
-  e = cudaMemcpyAsync(&err, ctr + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return noalloc_fail(OPMOS_ERR_CUDA, "heuristic kernel: %s", cudaGetErrorString(e));
-  if (err) return noalloc_fail((int)err, "heuristic kernel reported error %u", err);
-  return OPMOS_OK;
+  return noalloc_guarded("opmos_heuristic_noalloc", [&]() -> int {
+    if (!g || !h_out_device) return noalloc_fail(OPMOS_ERR_INVALID_ARG, "NULL graph or output");
+    if (goal >= g->n) return noalloc_fail(OPMOS_ERR_INVALID_ARG, "goal %u >= n = %u", goal, g->n);
+    const uint32_t D = d_used ? d_used : g->d;
+    if (D > g->d) return noalloc_fail(OPMOS_ERR_INVALID_ARG, "d_used %u > d %u", D, g->d);
+    if (g->n > kNoAllocMaxNodes)
+      return noalloc_fail(OPMOS_ERR_CAPACITY,
+                          "graph has %u nodes; the allocation-free heuristic handles at most %u "
+                          "(use opmos_heuristic)",
+                          g->n, kNoAllocMaxNodes);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(OPMOS_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    uint32_t* base = nullptr;
+    if (int rc = scratch_address(dev, &base)) return rc;
+    unsigned* ctr = base;
+    HJob* jobs = reinterpret_cast<HJob*>(base + kNoAllocCtrWords);
+    uint32_t* work = base + kNoAllocCtrWords + kNoAllocJobWords;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the array keeps the previous call's contents: the counters must restart
+    // at zero (worklists and flags are re-initialised by the kernel itself)
+    e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return noalloc_fail(OPMOS_ERR_CUDA, "clear counters: %s", cudaGetErrorString(e));
+    fill_jobs_kernel<<<1, 32, 0, s>>>(jobs, goal, D, h_out_device, g->n);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(OPMOS_ERR_CUDA, "job table: %s", cudaGetErrorString(e));
+    const unsigned blocks = D < kNoAllocBlocks ? D : kNoAllocBlocks;
+    e = launch_heuristic(g->dev, jobs, D, work, kNoAllocBlockWords, blocks, g->delta, ctr, ctr + 1, s);
+    if (e != cudaSuccess) return noalloc_fail(OPMOS_ERR_CUDA, "heuristic launch: %s", cudaGetErrorString(e));
+    unsigned err = 0;
+    e = cudaMemcpyAsync(&err, ctr + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return noalloc_fail(OPMOS_ERR_CUDA, "heuristic kernel: %s", cudaGetErrorString(e));
+    if (err) return noalloc_fail((int)err, "heuristic kernel reported error %u", err);
+    return OPMOS_OK;
+  });
 }
 
 }  // extern "C"

@@ -1,0 +1,34 @@
+"""Host-side parts of bench.py that need no GPU."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def test_cpu_batch_sample_runs_the_oracle_on_host_cores():
+    import bench
+    import synth
+    g, _ = synth.config1()
+    queries = [(0, 1023), (5, 900), (31, 992), (100, 700), (64, 1000), (2, 513)]
+    out = bench.cpu_batch_sample(g, queries, every=2, budget=0)
+    assert out["kind"] == "oracle" and out["unit"] == "queries/s" and out["value"] > 0
+    assert 1 <= out["cores"] <= 3
+    assert "3 of the 6 queries (1 in 2)" in out["sample"] and "0 over budget" in out["sample"]
+
+
+def test_cpu_batch_sample_reports_queries_over_budget():
+    import bench
+    import synth
+    g, _ = synth.config1()
+    out = bench.cpu_batch_sample(g, [(0, 1023), (0, 1023)], every=1, budget=50)
+    assert "2 over budget" in out["sample"]
+
+
+def test_traffic_digest_covers_the_kernel_sources_and_launch_options():
+    import bench
+    a = bench.kernel_source_digest((1024, 8, 32, 1))
+    assert len(a) == 16 and a == bench.kernel_source_digest((1024, 8, 32, 1))
+    assert a != bench.kernel_source_digest((512, 8, 32, 1))
+    assert all(os.path.exists(os.path.join(ROOT, f)) for f in bench.KERNEL_SOURCES)
+    assert isinstance(bench.TRAFFIC["bytes_per_launch"], int) and bench.TRAFFIC["bytes_per_launch"] > 0
