@@ -63,7 +63,7 @@ CPU_SAMPLE_LABELS = 1_500_000
 # valid only for the kernel sources and launch options whose digest is recorded
 # beside it: once either changes the figure is reported as null until it is
 # captured again.
-TRAFFIC = {"src_digest": "cfa52670abb65fa5", "bytes_per_launch": 303563520 + 695649792}
+TRAFFIC = {"src_digest": "6aeec19eeda886a1", "bytes_per_launch": 303563520 + 695649792}
 
 
 # the translation unit of the search kernels: the file and every header it includes
@@ -71,16 +71,28 @@ KERNEL_SOURCES = ("paper_2411_16667_gb300/csrc/search.cu", "paper_2411_16667_gb3
                   "paper_2411_16667_gb300/csrc/opmos_dev.cuh", "include/opmos.h")
 
 
-def kernel_source_digest(launch=()) -> str:
-    """sha256 over the search kernel's sources (names and contents) and the
-    launch options (window, lanes per label, tile, delta): what the kernel's
-    DRAM traffic on a given workload depends on."""
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments and trailing blanks (comments do not
+    change the compiled kernel)."""
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
+def kernel_source_digest(launch=(), read=None) -> str:
+    """sha256 over the search kernel's sources (names and contents without
+    comments) and the launch options (window, lanes per label, tile, delta):
+    what the kernel's DRAM traffic on a given workload depends on."""
     import hashlib
+    if read is None:
+        def read(rel):
+            with open(os.path.join(ROOT, rel)) as f:
+                return f.read()
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
         h.update(rel.encode())
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        h.update(strip_comments(read(rel)).encode())
     h.update(repr(tuple(int(x) for x in launch)).encode())
     return h.hexdigest()[:16]
 

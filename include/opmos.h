@@ -57,7 +57,10 @@ enum {
   OPMOS_ERR_OUT_OF_MEMORY = 3, /* device or host allocation failed */
   OPMOS_ERR_CAPACITY = 4,      /* a per-query arena (labels, frontiers, open list) filled up */
   OPMOS_ERR_BUDGET = 5,        /* the caller's label budget was exceeded */
-  OPMOS_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  OPMOS_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up, or a search
+                                  ran past its time limit (300 s of device time;
+                                  OPMOS_TIME_LIMIT_MS in the environment, read at
+                                  each call, overrides it) */
   OPMOS_ERR_CUDA = 7,          /* CUDA runtime error or no device */
   OPMOS_PENDING = 8            /* server: ticket not finished yet */
 };

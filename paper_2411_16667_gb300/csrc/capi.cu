@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -397,6 +398,18 @@ int search_status(unsigned st) {
 }
 
 constexpr unsigned long long kTimeLimitNs = 300ull * 1000 * 1000 * 1000;
+
+// Device time a search may take before it stops with OPMOS_ERR_TIMEOUT: 300 s,
+// or OPMOS_TIME_LIMIT_MS from the environment (read at each call) when that
+// is a positive integer.
+unsigned long long time_limit_ns() {
+  if (const char* e = std::getenv("OPMOS_TIME_LIMIT_MS")) {
+    char* end = nullptr;
+    const unsigned long long ms = std::strtoull(e, &end, 10);
+    if (end != e && *end == '\0' && ms > 0 && ms < (1ull << 40)) return ms * 1000000ull;
+  }
+  return kTimeLimitNs;
+}
 constexpr unsigned kBatchSlots = 192;  // concurrent queries of a batch
 constexpr size_t kOutWords = 64ull << 20;
 
@@ -456,7 +469,7 @@ int solve_one(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint
   P.tile = o.tile;
   P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, A.label_cap);
   P.flags = o.flags;
-  P.time_limit_ns = kTimeLimitNs;
+  P.time_limit_ns = time_limit_ns();
 
   int occ = search_occupancy(D, 0);
   if (occ <= 0) return fail(OPMOS_ERR_CUDA, "search kernel cannot be resident");
@@ -521,7 +534,7 @@ int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const st
   P.tile = o.tile;
   P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, pl.label_cap);
   P.flags = o.flags;
-  P.time_limit_ns = kTimeLimitNs;
+  P.time_limit_ns = time_limit_ns();
   std::vector<MSlot> hslots(slots);
   for (unsigned i = 0; i < slots; ++i) {
     MSlot& sl = hslots[i];
@@ -1143,7 +1156,7 @@ int opmos_server_create(const opmos_graph* const* graphs, uint32_t ngraphs, cons
       sl.P.tile = o.tile;
       sl.P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, pl.label_cap);
       sl.P.flags = o.flags;
-      sl.P.time_limit_ns = kTimeLimitNs;
+      sl.P.time_limit_ns = time_limit_ns();
       sl.state = SL_FREE;
     }
     std::vector<GraphDev> gd;

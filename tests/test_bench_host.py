@@ -32,3 +32,11 @@ def test_traffic_digest_covers_the_kernel_sources_and_launch_options():
     assert a != bench.kernel_source_digest((512, 8, 32, 1))
     assert all(os.path.exists(os.path.join(ROOT, f)) for f in bench.KERNEL_SOURCES)
     assert isinstance(bench.TRAFFIC["bytes_per_launch"], int) and bench.TRAFFIC["bytes_per_launch"] > 0
+
+
+def test_kernel_digest_ignores_comments_only():
+    import bench
+    a = "int f(int x) {  // add one\n  return x + 1; /* done */\n}\n"
+    b = "/* header */\nint f(int x) {\n  return x + 1;\n}\n"
+    c = "int f(int x) {\n  return x + 2;\n}\n"
+    assert bench.strip_comments(a) == bench.strip_comments(b) != bench.strip_comments(c)
