@@ -60,6 +60,18 @@ def test_brute_force_random_digraphs(seed):
     check_front(g, s, t, res.costs, res.paths)
 
 
+@pytest.mark.parametrize("d,seed", [(d, seed) for d in (6, 7, 8) for seed in (301, 304, 306, 308)])
+def test_brute_force_high_d(d, seed):
+    """The same pin at d = 6..8, the objective counts up to the library's
+    maximum (8-node graphs whose fronts hold 6 to 12 vectors)."""
+    n = 8
+    g = synth.random_digraph(seed, n, d, p=0.45, cmax=3)
+    s, t = 0, n - 1
+    res = oracle.solve(g, s, t)
+    assert _tuples(res.costs) == brute_front(g, s, t)
+    check_front(g, s, t, res.costs, res.paths)
+
+
 @pytest.mark.parametrize("rows,cols,d,seed", [(3, 3, 2, 1), (3, 4, 3, 2), (3, 4, 5, 3), (2, 5, 4, 4),
                                               (3, 3, 1, 5), (4, 3, 2, 6)])
 def test_brute_force_small_grids(rows, cols, d, seed):
