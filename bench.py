@@ -112,6 +112,16 @@ def fixture_stats() -> dict:
     return meta
 
 
+def oracle_count_bytes(st: dict, d: int) -> int:
+    """Algorithmic bytes of the sequential oracle's own counters, with the same
+    per-unit figures the device counters use: per extracted label 8d+12, per
+    candidate 4+8d, per compared vector 4d, per inserted label 4d+24, per
+    pruned label 4. The GPU gets no credit for the work it adds."""
+    pruned = st["pruned_open"] + st["pruned_open_goal"] + st["pruned_closed"] + st["pruned_p"]
+    return (st["extracted"] * (8 * d + 12) + st["candidates"] * (4 + 8 * d) + st["comparisons"] * 4 * d
+            + st["inserted"] * (4 * d + 24) + pruned * 4)
+
+
 def cpu_sample(g, s, t, budget=CPU_SAMPLE_LABELS) -> dict:
     """The oracle as it stands, single-threaded, on the first `budget` labels."""
     import oracle
@@ -622,6 +632,7 @@ def main():
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
     achieved = st["bytes"] / (search_ns / 1e9) / 1e9
+    achieved_oc = oracle_count_bytes(fx, g.d) / (search_ns / 1e9) / 1e9
     launch = (opt.window, opt.lanes_per_label, opt.tile, opt.delta)
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["src_digest"] == kernel_source_digest(launch) else None
     value = world * useful / (ms / 1e3)
@@ -636,6 +647,7 @@ def main():
         "search_steps": st["steps"], "step_ms_all": step_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "search_grid_kernel",
+                     "achieved_oracle_count": achieved_oc, "frac_oracle_count": achieved_oc / peak,
                      "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
                      else "fallback 6.8 TB/s"},
         "e2e": {"value": world * useful / statistics.median(e2e_t), "unit": UNIT, "h2d_bytes_per_step": int(h2d),

@@ -40,3 +40,15 @@ def test_kernel_digest_ignores_comments_only():
     b = "/* header */\nint f(int x) {\n  return x + 1;\n}\n"
     c = "int f(int x) {\n  return x + 2;\n}\n"
     assert bench.strip_comments(a) == bench.strip_comments(b) != bench.strip_comments(c)
+
+
+def test_oracle_count_bytes_of_the_headline_query():
+    """The per-unit figures applied to the committed oracle counters of the
+    256x256 d=3 query (written by tests/golden/make_golden.py)."""
+    import bench
+    fx = bench.fixture_stats()
+    d = 3
+    expect = (fx["extracted"] * 36 + fx["candidates"] * 28 + fx["comparisons"] * 12 + fx["inserted"] * 36
+              + 4 * (fx["pruned_open"] + fx["pruned_open_goal"] + fx["pruned_closed"] + fx["pruned_p"]))
+    assert bench.oracle_count_bytes(fx, d) == expect
+    assert 7.0e11 < expect < 7.5e11
