@@ -11,6 +11,7 @@ header of ``namoa_oracle.cpp``).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import dataclasses
 import os
@@ -48,23 +49,40 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _configure(lib):
+    u32, u64, p = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+    lib.oracle_heuristic.argtypes = [u32, u64, u32, p, p, p, u32, p]
+    lib.oracle_solve.argtypes = [u32, u64, u32, p, p, p, p, u32, u32, u64, ctypes.POINTER(p)]
+    lib.oracle_result_count.argtypes = [p]
+    lib.oracle_result_count.restype = u32
+    lib.oracle_result_costs.argtypes = [p, p]
+    lib.oracle_result_path_len.argtypes = [p, u32]
+    lib.oracle_result_path_len.restype = u32
+    lib.oracle_result_path.argtypes = [p, u32, p, p]
+    lib.oracle_result_stats.argtypes = [p, p]
+    lib.oracle_result_free.argtypes = [p]
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        u32, u64, p = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
-        lib.oracle_heuristic.argtypes = [u32, u64, u32, p, p, p, u32, p]
-        lib.oracle_solve.argtypes = [u32, u64, u32, p, p, p, p, u32, u32, u64, ctypes.POINTER(p)]
-        lib.oracle_result_count.argtypes = [p]
-        lib.oracle_result_count.restype = u32
-        lib.oracle_result_costs.argtypes = [p, p]
-        lib.oracle_result_path_len.argtypes = [p, u32]
-        lib.oracle_result_path_len.restype = u32
-        lib.oracle_result_path.argtypes = [p, u32, p, p]
-        lib.oracle_result_stats.argtypes = [p, p]
-        lib.oracle_result_free.argtypes = [p]
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+@contextlib.contextmanager
+def library(path: str):
+    """Run this binding on another build of ``namoa_oracle.cpp`` for the
+    duration of the block: tests that plant a mistake in a copy of the
+    oracle use it to show the pins catch the mistake."""
+    global _lib
+    saved = _lib
+    _lib = _configure(ctypes.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 def _ptr(a: np.ndarray):
