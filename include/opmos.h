@@ -108,7 +108,9 @@ typedef struct opmos_stats {
   uint64_t steps;          /* window steps */
   uint64_t frontier_cmp;   /* candidate-vs-frontier-entry vector comparisons */
   uint64_t p_cmp;          /* vector comparisons against P */
-  uint64_t bytes;          /* algorithmic bytes moved by the search (see DESIGN) */
+  uint64_t bytes;          /* algorithmic bytes of the search: per extracted label 8d+12, per
+                              candidate 4+8d, per compared frontier or P entry 4d, per
+                              inserted label 4d+24, per pruned label 4 */
   uint64_t heuristic_ns;   /* device time of the heuristic kernel(s) */
   uint64_t search_ns;      /* device time of the search kernel(s) */
   uint64_t total_ns;       /* host wall time of the call */

@@ -3,6 +3,7 @@ symbol include/opmos.h declares, and fails loudly without a device."""
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -53,3 +54,16 @@ def test_missing_library_fails_loudly(tmp_path):
             opmos.lib(str(tmp_path / "missing.so"))
     finally:
         opmos._lib = saved
+
+
+def test_plain_c_client_links_and_behaves(tmp_path):
+    """A C program built against the header alone and linked to the library:
+    defaults are filled in, and without a device compute calls fail with
+    OPMOS_ERR_CUDA and a message (with one, it checks a two-path front)."""
+    lib = pkg.build()
+    exe = tmp_path / "client"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "c_abi_client.c"), lib,
+                           f"-Wl,-rpath,{os.path.dirname(lib)}", "-o", str(exe)])
+    p = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert p.returncode == 0, f"exit {p.returncode}: {p.stdout} {p.stderr}"
