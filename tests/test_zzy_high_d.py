@@ -34,7 +34,7 @@ def test_high_d_single_and_batch(op, d):
     g = graphs[1]
     G = op.opmos_graph.from_synth(g)
     qs = [(0, 7), (1, 6), (2, 5), (3, 7), (0, 0)]
-    out = op.opmos_solve_batch(G, [s for s, _ in qs], [t for _, t in qs])
+    out = op.opmos_solve_batch(G, [s for s, _ in qs], [t for _, t in qs], mem_budget_bytes=4 << 30)
     for (s, t), (st, res) in zip(qs, out):
         assert st == op.OK
         assert np.array_equal(res.costs, oracle.solve(g, s, t).costs)

@@ -28,7 +28,7 @@ def test_time_limit_stops_the_search_with_timeout(op, monkeypatch):
     with pytest.raises(op.OpmosError) as e:
         op.opmos_solve(G, s, t, options=op._options(flags=op.FLAG_NO_PATHS))
     assert e.value.code == op.ERR_TIMEOUT
-    out = op.opmos_solve_batch(G, [s], [t])
+    out = op.opmos_solve_batch(G, [s], [t], mem_budget_bytes=8 << 30)
     assert out[0][0] == op.ERR_TIMEOUT and out[0][1] is None
     monkeypatch.delenv("OPMOS_TIME_LIMIT_MS")
     g1, q1 = synth.config1()
