@@ -31,6 +31,13 @@ Other workloads (--workload):
   serve             Poisson arrivals over the device-resident 32x32, 256x256 and
                     200k-node graphs, d ~ U{2..5} clamped, at three rates;
                     p50/p99 latency and queries/s beside one query per launch
+  order             ordered (priority) against FIFO windows of the same width:
+                    labels extracted, work ratio and time (Sec. 4, 7.1)
+
+The default line also carries, as extra keys, a config-4 batch subset timed
+as one launch and as one query per launch on the same queries ("batch", with
+the batch kernel's roofline) and the d = 12 time-expanded route
+("route_d12": time-to-front and work ratio against the oracle).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                        [--workload NAME]
@@ -67,8 +74,9 @@ TRAFFIC = {"src_digest": "6aeec19eeda886a1", "bytes_per_launch": 303563520 + 695
 
 
 # the translation unit of the search kernels: the file and every header it includes
-KERNEL_SOURCES = ("paper_2411_16667_gb300/csrc/search.cu", "paper_2411_16667_gb300/csrc/search.cuh",
-                  "paper_2411_16667_gb300/csrc/opmos_dev.cuh", "include/opmos.h")
+KERNEL_SOURCES = ("paper_2411_16667_gb300/csrc/search_impl.cuh", "paper_2411_16667_gb300/csrc/search_inst.cu",
+                  "paper_2411_16667_gb300/csrc/search.cuh", "paper_2411_16667_gb300/csrc/opmos_dev.cuh",
+                  "include/opmos.h")
 
 
 def strip_comments(src: str) -> str:
@@ -232,10 +240,23 @@ def dist_setup():
     return world, rank, local
 
 
-def shard_queries(n: int, rank: int, world: int) -> list[int]:
-    """Round-robin split of n independent queries over the ranks. Queries share
-    nothing, so the ranks exchange no data; only the timing is reduced."""
-    return list(range(rank, n, world))
+def shard_queries(n: int, rank: int, world: int, est=None) -> list[int]:
+    """Split of n independent queries over the ranks, round-robin in
+    decreasing order of estimated cost (``est``; index order without one),
+    so every rank gets a similar mix of long and short searches. Queries
+    share nothing, so the ranks exchange no data; only the timing is
+    reduced. Returns the rank's query indices in increasing order."""
+    order = list(range(n)) if est is None else sorted(range(n), key=lambda i: (-est[i], i))
+    return sorted(order[rank::world])
+
+
+def grid_distance(g, queries) -> list[int]:
+    """Chebyshev distance of each (start, goal) on a grid graph (an estimate
+    of the search's cost; 1 when the graph is not a grid)."""
+    cols = g.meta.get("cols")
+    if not cols or g.meta.get("windows"):
+        return [1] * len(queries)
+    return [max(abs(s // cols - t // cols), abs(s % cols - t % cols)) for s, t in queries]
 
 
 def max_over_ranks(x: float, device: str = "cuda") -> float:
@@ -254,6 +275,115 @@ def barrier():
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
         dist.barrier()
+
+
+ROUTES = os.path.join(ROOT, "tests", "golden", "routes.digests")
+ROUTE_D12 = (1, 6, 8, 24, 12)  # seed, rows, cols, windows, d of the default line's high-d route
+
+
+def route_digests() -> dict:
+    """Oracle digests of the time-expanded routes (tests/golden/make_golden.py routes)."""
+    out = {}
+    with open(ROUTES) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, gdig, s, t, count, labels, extracted, fdig = line.split()
+            out[name] = {"graph": gdig, "start": int(s), "goal": int(t), "count": int(count),
+                         "labels": int(labels), "extracted": int(extracted), "front": fdig}
+    return out
+
+
+def front_digest(costs) -> str:
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(costs, dtype="<u4").tobytes()).hexdigest()[:16]
+
+
+def route_leg(opmos, torch, stream, steps: int, window: int = 0, flags: int = 0) -> dict:
+    """The d = 12 time-expanded route (label processing dominates, Sec. 4):
+    time-to-front and work ratio against the oracle's committed counters."""
+    seed, rows, cols, windows, d = ROUTE_D12
+    g, q = synth.time_route(seed, rows, cols, windows, d)
+    ref = route_digests()[g.name]
+    if ref["graph"] != g.digest():
+        raise RuntimeError("regenerated route does not match its oracle digest")
+    G = opmos.opmos_graph.from_synth(g)
+    s, t = q[0]
+    opt = opmos.opmos_default_options(stream=stream.cuda_stream, window=window or None, flags=flags)
+    r = opmos.opmos_solve(G, s, t, options=opt)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(max(1, steps))]
+    for a, b in ev:
+        a.record(stream)
+        r = opmos.opmos_solve(G, s, t, options=opt)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    st = r.stats
+    return {"workload": f"{g.name}: time-expanded ship route, {rows}x{cols} cells x {windows} windows, "
+                        f"{g.n} nodes, {g.m} arcs, d = {d}",
+            "front_size": int(r.costs.shape[0]), "front_matches_oracle": front_digest(r.costs) == ref["front"],
+            "time_to_front_ms": ms, "search_kernel_ms": st["search_ns"] / 1e6,
+            "gpu_labels_extracted": st["extracted"], "oracle_labels_extracted": ref["extracted"],
+            "work_ratio": st["extracted"] / ref["extracted"],
+            "oracle_labels_per_s": ref["extracted"] / (ms / 1e3),
+            "frontier_cmp": st["frontier_cmp"], "p_cmp": st["p_cmp"], "steps": st["steps"]}
+
+
+BATCH_EVERY = 8        # the default line's batch subset: every 8th of the 1,024 config-4 queries
+BATCH_WINDOW = 1024    # the window the autotuner picks for this batch (bench.py --workload ship256-d5-batch)
+
+
+def batch_subset_leg(opmos, torch, stream, world: int, rank: int, steps: int) -> dict:
+    """Batched form against one query per launch on the SAME queries: a fixed
+    subset of the 5-objective ship-grid batch (config 4), run as one
+    continuous-batching launch and as a loop of single-query launches, with
+    the batch kernel's roofline (algorithmic bytes of the launch over its
+    device time). Under torchrun each rank takes its share of the subset."""
+    g, q = synth.config4(1)
+    sub = q[::BATCH_EVERY]
+    mine = shard_queries(len(sub), rank, world, grid_distance(g, sub))
+    qs = [sub[i] for i in mine]
+    G = opmos.opmos_graph.from_synth(g)
+    starts, goals = [s for s, _ in qs], [t for _, t in qs]
+    bopt = opmos._options(stream=stream.cuda_stream, window=BATCH_WINDOW, flags=opmos.FLAG_GRAPH)
+    sopt = opmos.opmos_default_options(stream=stream.cuda_stream)
+    opmos.opmos_solve_batch(G, starts, goals, options=bopt)  # warm-up
+    torch.cuda.synchronize()
+    times, out = [], None
+    for _ in range(max(1, steps)):
+        barrier()
+        t0 = time.perf_counter()
+        out = opmos.opmos_solve_batch(G, starts, goals, options=bopt)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    bsec = max_over_ranks(statistics.median(times))
+    barrier()
+    t0 = time.perf_counter()
+    singles = [opmos.opmos_solve(G, s, t, options=sopt) for s, t in qs]
+    torch.cuda.synchronize()
+    ssec = max_over_ranks(time.perf_counter() - t0)
+    ok = sum(1 for st, r in out if st == opmos.OK)
+    same = all(st == opmos.OK and np.array_equal(r.costs, x.costs) for (st, r), x in zip(out, singles))
+    rs = [r for _, r in out if r is not None]
+    launches = {}
+    for r in rs:  # queries re-run in a later launch carry that launch's time
+        launches.setdefault(r.stats["search_ns"], []).append(r.stats["bytes"])
+    kern_ns = max(launches, key=lambda k: len(launches[k]))
+    kbytes = sum(launches[kern_ns])
+    peak, src = _peak()
+    ach = kbytes / (kern_ns / 1e9) / 1e9
+    nq = len(sub)
+    return {"workload": f"ship256-d5-batch subset: {nq} of the 1,024 config-4 queries (every {BATCH_EVERY}th), "
+                        f"5 objectives, seed 1, window {BATCH_WINDOW}",
+            "queries": nq, "queries_ok": ok, "same_fronts_as_single": same,
+            "batched_qps": nq / bsec, "one_query_per_launch_qps": nq / ssec,
+            "batched_over_single": ssec / bsec, "batch_wall_ms": 1e3 * bsec, "single_loop_ms": 1e3 * ssec,
+            "batch_kernel_ms": kern_ns / 1e6,
+            "labels_per_s": sum(r.stats["extracted"] for r in rs) / (kern_ns / 1e9),
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "kernel": f"multi_kernel<5>", "peak_source": src,
+                         "bytes": kbytes, "queries_in_launch": len(launches[kern_ns])}}
 
 
 def run_reference(args, world, rank):
@@ -326,7 +456,7 @@ def run_batch(args, opmos, torch, stream):
     world, rank, _ = dist_setup()
     g, q = synth.config4(1)
     G = opmos.opmos_graph.from_synth(g)
-    mine = shard_queries(len(q), rank, world)
+    mine = shard_queries(len(q), rank, world, grid_distance(g, q))
     starts = [q[i][0] for i in mine]
     goals = [q[i][1] for i in mine]
     # autotuned on a calibration subset (every 32nd query), outside the timed region
@@ -439,6 +569,47 @@ def run_road_batch(args, opmos, torch, stream):
                       "clocks": clk.summary()}), flush=True)
 
 
+def run_order(args, opmos, torch, stream):
+    """Ordered (lexicographic priority) windows against FIFO windows (Sec. 4
+    and 7.1: PQ versus FIFO) at the same width: work (labels extracted, work
+    ratio against the oracle) and time on the config-2 query, the d = 12
+    route, and the config-4 batch subset."""
+    fx = fixture_stats()
+    g, q = synth.config2()
+    G = opmos.opmos_graph.from_synth(g)
+    rows = []
+    for w in (256, 1024, 4096):
+        for name, flags in (("ordered", 0), ("fifo", opmos.FLAG_FIFO)):
+            opt = opmos.opmos_default_options(stream=stream.cuda_stream, window=w, flags=flags)
+            r = opmos.opmos_solve(G, *q[0], options=opt)
+            ok = r.costs.shape[0] == fx["count"]
+            rows.append({"workload": "ship256-d3", "order": name, "window": w, "front_ok": ok,
+                         "search_ms": r.stats["search_ns"] / 1e6, "steps": r.stats["steps"],
+                         "extracted": r.stats["extracted"], "work_ratio": r.stats["extracted"] / fx["extracted"]})
+            print(json.dumps(rows[-1]), flush=True)
+    for w in (256, 1024):
+        for name, flags in (("ordered", 0), ("fifo", opmos.FLAG_FIFO)):
+            leg = route_leg(opmos, torch, stream, 1, window=w, flags=flags)
+            rows.append({"workload": "route6x8x24-d12", "order": name, "window": w,
+                         "front_ok": leg["front_matches_oracle"], "search_ms": leg["search_kernel_ms"],
+                         "steps": leg["steps"], "extracted": leg["gpu_labels_extracted"],
+                         "work_ratio": leg["work_ratio"]})
+            print(json.dumps(rows[-1]), flush=True)
+    g4, q4 = synth.config4(1)
+    G4 = opmos.opmos_graph.from_synth(g4)
+    sub = q4[::BATCH_EVERY]
+    for name, flags in (("ordered", 0), ("fifo", opmos.FLAG_FIFO)):
+        opt = opmos._options(stream=stream.cuda_stream, window=BATCH_WINDOW, flags=flags)
+        out = opmos.opmos_solve_batch(G4, [s for s, _ in sub], [t for _, t in sub], options=opt)
+        rs = [r for _, r in out if r is not None]
+        rows.append({"workload": f"ship256-d5-batch subset ({len(sub)} queries)", "order": name,
+                     "window": BATCH_WINDOW, "queries_ok": sum(1 for st_, _ in out if st_ == opmos.OK),
+                     "batch_kernel_ms": max(r.stats["search_ns"] for r in rs) / 1e6,
+                     "extracted": sum(r.stats["extracted"] for r in rs)})
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"metric": "work and time, ordered vs FIFO windows", "rows": len(rows)}), flush=True)
+
+
 def serve_queries(n, seed=5):
     """Config-5 query stream over configs 1-3: graph uniform, d ~ U{2..5}
     clamped to the graph's objective count, start/goal as in each config."""
@@ -539,11 +710,14 @@ def main():
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--cpu-labels", type=int, default=CPU_SAMPLE_LABELS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch-leg", action="store_true",
+                    help="leave the config-4 batch subset out of the default line")
     ap.add_argument("--serve-queries", type=int, default=48)
     ap.add_argument("--serve-label-budget", type=int, default=2_000_000)
     ap.add_argument("--road-label-budget", type=int, default=1_000_000)
     ap.add_argument("--workload", default="ship256-d3",
-                    choices=["ship256-d3", "ship128-d3", "ship256-d5-batch", "road200k-d4-batch", "serve"])
+                    choices=["ship256-d3", "ship128-d3", "ship256-d5-batch", "road200k-d4-batch", "serve",
+                             "order"])
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -568,6 +742,8 @@ def main():
                     return run_batch(args, opmos, torch, stream)
                 if args.workload == "road200k-d4-batch":
                     return run_road_batch(args, opmos, torch, stream)
+                if args.workload == "order":
+                    return run_order(args, opmos, torch, stream)
                 return run_serve(args, opmos, torch, stream)
         finally:
             if world > 1:
@@ -621,6 +797,9 @@ def main():
             e2e_t.append(time.perf_counter() - t0)
             d2h = r.costs.nbytes + sum(a.nbytes // 2 + b.nbytes for a, b in r.paths)  # device words are u32
 
+        batch = None if args.no_batch_leg else batch_subset_leg(opmos, torch, stream, world, rank, 1)
+        route = None if args.no_batch_leg else route_leg(opmos, torch, stream, 3)
+
     search_ns = statistics.median(x["search_ns"] for x in stats)
     heur_ns = statistics.median(x["heuristic_ns"] for x in stats)
     st = stats[-1]
@@ -654,7 +833,15 @@ def main():
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
+        "open_scanned_per_step": st["open_scanned"] / max(1, st["steps"]),
+        "longest_task_us_per_step": {k: v / 1e3 / max(1, st["steps"]) for k, v in
+                                     zip(("block_merge", "warp_merge", "extraction"), st["longest_task_ns"])},
+        "window": opt.window,
     }
+    if batch is not None:
+        line["batch"] = batch
+    if route is not None:
+        line["route_d12"] = route
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample(g, s, t, args.cpu_labels)
     if rank == 0:

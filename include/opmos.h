@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define OPMOS_MAX_D 8
+#define OPMOS_MAX_D 16
 
 enum {
   OPMOS_OK = 0,
@@ -73,9 +73,12 @@ typedef struct opmos_server opmos_server;
 /* Search options. Zero in any field selects the library default. */
 typedef struct opmos_options {
   uint32_t window;           /* W: target number of labels extracted per step (the NUM_POP of
-                                Algorithm 2, Sec. 5). Steps take whole F[0] buckets, so a step
-                                may take fewer (never more than 4W). Default 1024 (single query),
-                                256 (batch). */
+                                Algorithm 2, Sec. 5). Steps take whole histogram bins of
+                                (F[0], F[1]), so a step may take fewer, or more when the lowest
+                                bin alone holds more (never more than max(4W, 16384); past that
+                                bound which labels of the bin a step takes depends on thread
+                                timing, the front does not). Default 1024 (single query), 256
+                                (batch). */
   uint32_t lanes_per_label;  /* threads that expand one label's out-arcs: 4, 8, 16 or 32.
                                 Default 8. */
   uint32_t tile;             /* frontier growth granule in entries (multiple of 32). Default 32. */
@@ -95,6 +98,10 @@ typedef struct opmos_options {
 #define OPMOS_FLAG_GRAPH 2u        /* batch: capture each launch (input uploads from pinned staging,
                                       the persistent kernel, result downloads) into a CUDA graph and
                                       replay it; a capture failure is reported as OPMOS_ERR_CUDA */
+#define OPMOS_FLAG_FIFO 4u         /* relaxed order: OPEN is a first-in first-out queue and each step
+                                      takes its W oldest entries instead of the W lexicographically
+                                      lowest F (the FIFO alternative of Sec. 4 and 7.1). The front is
+                                      the same; the labels extracted are more. */
 
 /* Counters of one solve (sums over a batch for batch results). Sec. 6.2 lists
  * the paper's counters: extractions, candidate labels, solutions. */
@@ -114,10 +121,21 @@ typedef struct opmos_stats {
   uint64_t heuristic_ns;   /* device time of the heuristic kernel(s) */
   uint64_t search_ns;      /* device time of the search kernel(s) */
   uint64_t total_ns;       /* host wall time of the call */
-  uint64_t phase_ns[4];    /* device time per search phase (histogram, extract+expand, merge,
-                              output), as seen by the leading thread, barrier waits included */
+  uint64_t phase_ns[4];    /* device time of the search as seen by the leading thread:
+                              [0] window selection and step control, [1] merge of window i
+                              overlapped with extraction and expansion of window i+1,
+                              [2] end of step (histogram flush, barrier wait), [3] output */
   uint64_t goal_inserted;  /* goal labels accepted into P during the search (before the final
                               removal of dominated members) */
+  uint64_t open_scanned;   /* OPEN entries read by the extraction scans, summed over steps
+                              (an entry read by two passes of one step counts twice) */
+  uint64_t open_rewritten; /* OPEN entries copied forward to the next step's OPEN array */
+  uint64_t list_candidates; /* candidates beyond the slots a node has per step (32 in a
+                               batch, 128 for a single query), merged from the node's list */
+  uint64_t longest_task_ns[3]; /* summed over steps: the step's longest whole-block merge of a
+                                  node with a large frontier, longest one-warp node merge, and
+                                  longest extraction work item (the step's critical path) */
+  uint64_t heavy_merges;   /* node merges done by a whole block (frontier >= 512 entries) */
 } opmos_stats;
 
 /* Fill *opt with the defaults (all fields explicit). */
@@ -158,8 +176,13 @@ OPMOS_API void opmos_heuristic_destroy(opmos_heur* h);
  *     looks up its address (cudaGetSymbolAddress) with that device current;
  *     make that first call before any stream capture. Every call reuses the
  *     same array, so calls that overlap on the GPU (other threads, other
- *     streams) race: serialise them. The call returns when the result is
- *     complete. Errors: INVALID_ARG, CAPACITY, TIMEOUT, CUDA. */
+ *     streams) race: serialise them. Each call synchronises `stream` (it
+ *     reads the kernel's status word back) and returns when the result is
+ *     complete.
+ *   Speed: the fixed array holds the worklists of 2 thread blocks, so the
+ *     d_used single-objective searches run at most 2 at a time (opmos_heuristic
+ *     runs all of them at once); for d_used > 2 the call takes up to
+ *     ceil(d_used / 2) times as long. Errors: INVALID_ARG, CAPACITY, TIMEOUT, CUDA. */
 OPMOS_API int opmos_heuristic_noalloc(const opmos_graph* g, uint32_t goal, uint32_t d_used,
                                       uint32_t* h_out_device, void* stream);
 

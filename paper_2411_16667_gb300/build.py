@@ -2,7 +2,9 @@
 
 Each translation unit under ``csrc/`` is compiled by nvcc in parallel, then
 linked into one shared library whose exported symbols are exactly the C ABI
-of ``include/opmos.h``.
+of ``include/opmos.h``. The search kernels (``search_inst.cu``) are compiled
+once per group of objective counts, so the 16 instantiations build side by
+side.
 """
 from __future__ import annotations
 
@@ -22,8 +24,27 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "-I", INCLUDE, "-I", CSRC]
 
 
+# objective counts compiled into one object each; the single-query and
+# multi-query kernels of a count take roughly the same time to compile
+D_GROUPS = ((1, 2), (3, 3), (4, 4), (5, 6), (7, 8), (9, 10), (11, 12), (13, 14), (15, 16))
+INST = "search_inst.cu"
+
+
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+
+
+def units():
+    """(source, extra flags, object name) for every object of the library."""
+    out = []
+    for src in sources():
+        name = os.path.basename(src)
+        if name == INST:
+            for a, b in D_GROUPS:
+                out.append((src, [f"-DOPMOS_D_FIRST={a}", f"-DOPMOS_D_LAST={b}"], f"{name}.d{a}_{b}.o"))
+        else:
+            out.append((src, [], name + ".o"))
+    return out
 
 
 def _deps_mtime():
@@ -31,8 +52,8 @@ def _deps_mtime():
     return max(os.path.getmtime(f) for f in files)
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], objname: str) -> str:
+    obj = os.path.join(BUILD, objname)
     cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -46,8 +67,11 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), sources()))
+    jobs = units()
+    # the instantiation groups first: they are the long ones
+    jobs.sort(key=lambda u: os.path.basename(u[0]) != INST)
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(lambda u: _compile(u[0], extra + u[1], u[2]), jobs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

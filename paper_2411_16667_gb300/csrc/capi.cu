@@ -200,26 +200,34 @@ int check_options(const opmos_options& o, const opmos_graph* g, uint32_t* d_used
   return OPMOS_OK;
 }
 
+constexpr uint32_t kWindowCapMin = 16384;  // labels a window may hold at least
+
 // Sizes of one query arena for a given byte budget.
 struct ArenaPlan {
-  uint32_t label_cap, open_cap, win_cap, cand_cap, plog_cap;
+  uint32_t label_cap, open_cap, win_cap, cand_cap, plog_cap, nslots;
   unsigned long long fpool_words;
   size_t bytes;
 };
 
 int plan_arena(const opmos_graph* g, uint32_t D, uint32_t window, size_t budget, bool batch, ArenaPlan* pl) {
   const size_t n = g->n;
-  pl->win_cap = 4 * window;
+  // a step takes whole histogram bins, so it may take more than W when the
+  // lowest bin alone holds more; beyond win_cap the part it takes would
+  // depend on thread timing (the front would not), hence the generous cap
+  pl->win_cap = std::max<uint32_t>(4 * window, kWindowCapMin);
   pl->cand_cap = pl->win_cap * std::max<uint32_t>(g->maxdeg, 1);
   pl->plog_cap = batch ? (1u << 16) : (1u << 20);
   const size_t ptiles = pl->plog_cap / 32 + 1;
-  size_t fixed = (n + 1) * (8 + 4 + 4 + 4 + 4 + 4 * kNodeSlots) + 2 * kNB * 4 + (size_t)pl->win_cap * 4 +
-                 (size_t)pl->cand_cap * (16 + 4 * D + 4) + (size_t)pl->plog_cap * 4 * D +
-                 2 * ((size_t)pl->plog_cap + ptiles) * 4 * D + 64 * 256;
+  // per node: fbase, fcount, fcap, then per candidate set ncand, node_head, slots;
+  // per candidate (two sets): node, parent, arc, list link, two touched entries, cost vector
+  pl->nslots = batch ? kNodeSlots : kNodeSlotsGrid;
+  size_t fixed = (n + 1) * (8 + 4 + 4 + 2 * (4 + 4 + 4 + 4 * (size_t)pl->nslots)) + 3 * kNB * 4 +
+                 2 * (size_t)pl->cand_cap * (24 + 4 * D) + (size_t)pl->plog_cap * 4 * D +
+                 2 * ((size_t)pl->plog_cap + ptiles) * 4 * D + kPSMax * 4 + 64 * 256;
   if (budget < fixed + (8u << 20))
     return fail(OPMOS_ERR_CAPACITY, "arena budget %zu too small (fixed part %zu)", budget, fixed);
   const size_t rem = budget - fixed;
-  const size_t per_label = 4 * D + 17;
+  const size_t per_label = 4 * D + 20;  // cost vector, node, parent, arc, P-log mark, death step
   size_t labels = rem * 30 / 100 / per_label;
   labels = std::min<size_t>(labels, 0xFFFFFF00u);
   pl->label_cap = (uint32_t)labels;
@@ -236,24 +244,28 @@ void layout_arena(const opmos_graph* g, uint32_t D, const ArenaPlan& pl, char* b
   A->fbase = carve<uint64_t>(p, n);
   A->fcount = carve<uint32_t>(p, n);
   A->fcap = carve<uint32_t>(p, n);
-  A->node_head = carve<int32_t>(p, n);
-  A->ncand = carve<uint32_t>(p, n);
-  A->cslot = carve<int32_t>(p, n * kNodeSlots);
-  A->hist = carve<uint32_t>(p, 2 * kNB);
-  A->window = carve<uint32_t>(p, pl.win_cap);
-  A->cnode = carve<uint32_t>(p, pl.cand_cap);
-  A->cparent = carve<uint32_t>(p, pl.cand_cap);
-  A->cedge = carve<uint32_t>(p, pl.cand_cap);
-  A->cnext = carve<int32_t>(p, pl.cand_cap);
-  A->touched = carve<uint32_t>(p, pl.cand_cap);
-  A->cg = carve<uint32_t>(p, (size_t)pl.cand_cap * D);
+  for (int b = 0; b < 2; ++b) {
+    CandSet& cs = A->cs[b];
+    cs.ncand = carve<uint32_t>(p, n);
+    cs.node_head = carve<int32_t>(p, n);
+    cs.hflag = carve<uint32_t>(p, n);
+    cs.cslot = carve<int32_t>(p, n * pl.nslots);
+    cs.cnode = carve<uint32_t>(p, pl.cand_cap);
+    cs.cparent = carve<uint32_t>(p, pl.cand_cap);
+    cs.cedge = carve<uint32_t>(p, pl.cand_cap);
+    cs.cnext = carve<int32_t>(p, pl.cand_cap);
+    cs.touched = carve<uint32_t>(p, 2 * (size_t)pl.cand_cap);
+    cs.cg = carve<uint32_t>(p, (size_t)pl.cand_cap * D);
+  }
+  A->hist = carve<uint32_t>(p, 3 * kNB);
+  A->prank = carve<uint32_t>(p, kPSMax);
   A->plog = carve<uint32_t>(p, (size_t)pl.plog_cap * D);
   A->lg = carve<uint32_t>(p, (size_t)pl.label_cap * D);
   A->lnode = carve<uint32_t>(p, pl.label_cap);
   A->lparent = carve<uint32_t>(p, pl.label_cap);
   A->ledge = carve<uint32_t>(p, pl.label_cap);
   A->lpver = carve<uint32_t>(p, pl.label_cap);
-  A->lstatus = carve<uint8_t>(p, pl.label_cap);
+  A->ldead = carve<uint32_t>(p, pl.label_cap);
   for (int b = 0; b < 2; ++b) {
     A->okey[b] = carve<uint64_t>(p, pl.open_cap);
     A->oid[b] = carve<uint32_t>(p, pl.open_cap);
@@ -267,6 +279,7 @@ void layout_arena(const opmos_graph* g, uint32_t D, const ArenaPlan& pl, char* b
   A->cand_cap = pl.cand_cap;
   A->plog_cap = pl.plog_cap;
   A->fpool_words = pl.fpool_words;
+  A->nslots = pl.nslots;
 }
 
 int compute_heuristic(const opmos_graph* g, uint32_t D, const uint32_t* goals, uint32_t ngoals, uint32_t* h,
@@ -325,11 +338,18 @@ void fill_stats(opmos_stats* s, const QResult& R, uint32_t D) {
   s->steps = R.stats[S_STEPS];
   s->frontier_cmp = R.stats[S_FCMP];
   s->p_cmp = R.stats[S_PCMP];
-  s->phase_ns[0] = R.stats[S_THIST];
-  s->phase_ns[1] = R.stats[S_TEXPAND];
-  s->phase_ns[2] = R.stats[S_TMERGE];
+  s->phase_ns[0] = R.stats[S_TSEL];
+  s->phase_ns[1] = R.stats[S_TWORK];
+  s->phase_ns[2] = R.stats[S_TSYNC];
   s->phase_ns[3] = R.stats[S_TOUT];
   s->goal_inserted = R.stats[S_GOALINS];
+  s->open_scanned = R.stats[S_OSCAN];
+  s->open_rewritten = R.stats[S_OKEEP];
+  s->list_candidates = R.stats[S_OVF];
+  s->longest_task_ns[0] = R.stats[S_MAXH];
+  s->longest_task_ns[1] = R.stats[S_MAXL];
+  s->longest_task_ns[2] = R.stats[S_MAXX];
+  s->heavy_merges = R.stats[S_NHEAVY];
   // algorithmic bytes: per extracted label 8d+12 (g, node, rowptr pair, F key),
   // per candidate 4+8d (col, cost, h), per compared frontier/P entry 4d, per
   // inserted label 4d+24 (label record, frontier slot, OPEN entry), per prune 4.
@@ -338,9 +358,12 @@ void fill_stats(opmos_stats* s, const QResult& R, uint32_t D) {
              s->inserted * (4 * d + 24) + s->pruned * 4;
 }
 
-// Copy one query's output region to a host result.
+// Copy one query's output region to a host result. The kernel wrote Dk
+// columns per cost vector; the query uses the first D of them (the rest are
+// the zero objectives a query with fewer objectives than its kernel carries).
 int take_result(const QResult& R, uint32_t D, bool paths, const uint32_t* words, cudaStream_t s,
-                opmos_result** out) {
+                opmos_result** out, uint32_t Dk = 0) {
+  if (Dk == 0) Dk = D;
   auto* r = new (std::nothrow) opmos_result;
   if (!r) return fail(OPMOS_ERR_OUT_OF_MEMORY, "host allocation");
   r->count = R.count;
@@ -349,7 +372,7 @@ int take_result(const QResult& R, uint32_t D, bool paths, const uint32_t* words,
   const size_t k = R.count;
   r->costs.resize(k * D);
   r->offs.resize(k + 1);
-  std::vector<uint32_t> tmp(k * D + k + 1);
+  std::vector<uint32_t> tmp(k * Dk + k + 1);
   if (!tmp.empty()) {
     cudaError_t e = cudaMemcpyAsync(tmp.data(), words + R.off, tmp.size() * 4, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) {
@@ -371,8 +394,9 @@ int take_result(const QResult& R, uint32_t D, bool paths, const uint32_t* words,
     delete r;
     return cuda_fail(e, "result copy");
   }
-  std::copy(tmp.begin(), tmp.begin() + k * D, r->costs.begin());
-  std::copy(tmp.begin() + k * D, tmp.end(), r->offs.begin());
+  for (size_t i = 0; i < k; ++i)
+    std::copy(tmp.begin() + i * Dk, tmp.begin() + i * Dk + D, r->costs.begin() + i * D);
+  std::copy(tmp.begin() + k * Dk, tmp.end(), r->offs.begin());
   if (paths && R.total) {
     r->nodes.assign(pw.begin(), pw.begin() + R.total);
     r->edges.resize(R.total - k);
@@ -411,6 +435,11 @@ unsigned long long time_limit_ns() {
   return kTimeLimitNs;
 }
 constexpr unsigned kBatchSlots = 192;  // concurrent queries of a batch
+// P-index rebuild thresholds (log growth beyond 32 + count >> grow): the
+// whole grid ranks a single query's index fast; a multi-query slot has only
+// its share of the blocks, so it rebuilds less often.
+constexpr uint32_t kGridIndexGrow = 6;
+constexpr uint32_t kMultiIndexGrow = 4;
 constexpr size_t kOutWords = 64ull << 20;
 
 int solve_one(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint32_t goal, const opmos_options& o,
@@ -469,9 +498,11 @@ int solve_one(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint
   P.tile = o.tile;
   P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, A.label_cap);
   P.flags = o.flags;
+  P.qd = D;
+  P.ps_grow = kGridIndexGrow;
   P.time_limit_ns = time_limit_ns();
 
-  int occ = search_occupancy(D, 0);
+  int occ = search_occupancy(D);
   if (occ <= 0) return fail(OPMOS_ERR_CUDA, "search kernel cannot be resident");
   const unsigned blocks = (unsigned)di.sms;  // one block of kGridThreads per SM
   cudaEvent_t e0, e1;
@@ -519,7 +550,7 @@ int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const st
   const DevInfo di = device_info();
   cudaStream_t s = (cudaStream_t)o.stream;
   const uint32_t nq = (uint32_t)qlist.size();
-  const int occ = multi_occupancy();
+  const int occ = multi_occupancy(D);
   if (occ <= 0) return fail(OPMOS_ERR_CUDA, "multi-query kernel cannot be resident");
   const unsigned blocks = (unsigned)di.sms * (unsigned)std::min(occ, 2);
   ArenaPlan pl;
@@ -534,6 +565,8 @@ int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const st
   P.tile = o.tile;
   P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, pl.label_cap);
   P.flags = o.flags;
+  P.qd = D;
+  P.ps_grow = kMultiIndexGrow;
   P.time_limit_ns = time_limit_ns();
   std::vector<MSlot> hslots(slots);
   for (unsigned i = 0; i < slots; ++i) {
@@ -637,7 +670,7 @@ int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const st
       cudaMemsetAsync(dres, 0, b_r, s);
       cudaMemcpyAsync(dslots, p_sl, b_sl, cudaMemcpyHostToDevice, s);
       cudaMemcpyAsync(dqs, p_q, b_q, cudaMemcpyHostToDevice, s);
-      const cudaError_t el = launch_multi(dslots, ctls, slots, dqs, hctl, dgraphs, dres, nullptr, M, blocks, s);
+      const cudaError_t el = launch_multi(D, dslots, ctls, slots, dqs, hctl, dgraphs, dres, nullptr, M, blocks, s);
       cudaMemcpyAsync(p_r, dres, b_r, cudaMemcpyDeviceToHost, s);
       cudaMemcpyAsync(p_M2, M, sizeof(MCtl), cudaMemcpyDeviceToHost, s);
       e = cudaStreamEndCapture(s, &graph);
@@ -677,7 +710,7 @@ int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const st
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    cudaError_t e = launch_multi(dslots, ctls, slots, dqs, hctl, dgraphs, dres, nullptr, M, blocks, s);
+    cudaError_t e = launch_multi(D, dslots, ctls, slots, dqs, hctl, dgraphs, dres, nullptr, M, blocks, s);
     cudaEventRecord(e1, s);
     cudaError_t e2 =
         e == cudaSuccess ? cudaMemcpyAsync(hres.data(), dres, nq * sizeof(QResult), cudaMemcpyDeviceToHost, s) : e;
@@ -1156,6 +1189,8 @@ int opmos_server_create(const opmos_graph* const* graphs, uint32_t ngraphs, cons
       sl.P.tile = o.tile;
       sl.P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, pl.label_cap);
       sl.P.flags = o.flags;
+      sl.P.qd = sv->dmax;
+      sl.P.ps_grow = kMultiIndexGrow;
       sl.P.time_limit_ns = time_limit_ns();
       sl.state = SL_FREE;
     }
@@ -1176,10 +1211,10 @@ int opmos_server_create(const opmos_graph* const* graphs, uint32_t ngraphs, cons
       server_free(sv);
       return cuda_fail(e, "server set-up");
     }
-    const int occ = multi_occupancy();
+    const int occ = multi_occupancy(sv->dmax);
     const unsigned full = (unsigned)di.sms * (unsigned)std::min(occ, 2);
     sv->blocks = full > 2 * kServeHeurBlocks ? full - 2 * kServeHeurBlocks : std::max(1u, full / 2);
-    e = launch_multi(dslots, ctls, sv->nslots, (MQuery*)dev_of(sv->hq), (unsigned*)dev_of(sv->hctl), dgraphs,
+    e = launch_multi(sv->dmax, dslots, ctls, sv->nslots, (MQuery*)dev_of(sv->hq), (unsigned*)dev_of(sv->hctl), dgraphs,
                      (QResult*)dev_of(sv->hres), (unsigned*)dev_of(sv->hdone), M, sv->blocks, sv->kstream);
     if (e != cudaSuccess) {
       server_free(sv);
@@ -1254,7 +1289,8 @@ int opmos_server_poll(opmos_server* sv, uint64_t ticket, opmos_result** out) {
     int rc = (int)R.status;
     if (rc == OPMOS_OK) {
       opmos_result* r = nullptr;
-      rc = take_result(R, sv->qd[idx], !(sv->o.flags & OPMOS_FLAG_NO_PATHS), sv->pool_words[slot], sv->hstream, &r);
+      rc = take_result(R, sv->qd[idx], !(sv->o.flags & OPMOS_FLAG_NO_PATHS), sv->pool_words[slot], sv->hstream, &r,
+                       sv->dmax);
       if (rc == OPMOS_OK) {
         fill_stats(&r->stats, R, sv->qd[idx]);
         *out = r;

@@ -3,13 +3,19 @@
 // Data layout (all device-resident, structure of arrays):
 //   graph      rowptr[n+1], col[m], cost[k*m + e]; reversed CSR rrowptr/rsrc/rcost
 //   heuristic  h[k*n + v]                      (Sec. 4 ideal point)
-//   labels     lg[k*label_cap + id], lnode, lparent, ledge, lstatus, lpver
+//   labels     lg[k*label_cap + id], lnode, lparent, ledge, lpver, ldead (the
+//              step in which the label was pruned, kAlive while it is not)
 //   frontier   per node v: a contiguous block at fpool[fbase[v]] of capacity
 //              fcap[v]: costs [k*cap + i] then label ids [d*cap + i]; fcount[v]
 //              live entries (alpha(v) = G_OP(v) u G_CL(v), Sec. 3)
 //   OPEN       two unsorted arrays of 64-bit keys (F[0] << 32 | F[1]) with
-//              label ids beside them, bucketed through a per-step histogram
-//              (the batch extraction of Algorithm 2): the lowest F[0] bucket is split by F[1]
+//              label ids beside them (the step's OPEN and the next one), and a
+//              histogram of each by lexicographic bucket of (F[0], F[1]) (the
+//              ordered batch extraction of Algorithm 2); with OPMOS_FLAG_FIFO
+//              the first array is a ring read oldest first instead
+//   candidates two sets (step parity): the candidates of one window, grouped by
+//              target node (the first nslots per node in slots, the rest in a
+//              per-node list)
 //   P log      append-only list of every goal cost vector ever accepted; its
 //              prefix is a valid filter for "F dominated by P" (Algorithm 1)
 //   P index    a snapshot of P sorted along a Z-order curve over objectives
@@ -24,14 +30,19 @@
 namespace opmos {
 
 constexpr uint32_t kInf = 0xFFFFFFFFu;
+constexpr uint32_t kAlive = 0xFFFFFFFFu;  // ldead of a label that has not been pruned
 constexpr int32_t kNil = -1;
-constexpr int kNB = 2048;   // open-list histogram buckets per step
-constexpr int kNB1 = 1024;  // of which sub-buckets (by F[1]) of the lowest F[0] bucket
-constexpr unsigned kPSMax = 32768;  // largest P indexed by the sorted snapshot
+constexpr int kNB = 4096;    // histogram bins of one OPEN array
+constexpr int kRows = 8;     // lowest F[0] buckets of a histogram, each split by F[1]
+constexpr int kSub = 256;    // F[1] sub-bins of each of them
+constexpr int kSplit = kRows * kSub;  // bins [0, kSplit) are split, [kSplit, kNB-1) whole, kNB-1 overflow
+constexpr unsigned kChunk = 32;       // OPEN entries per extraction work item
+constexpr unsigned kRankQ = 1024;     // P entries per rank work item of an index rebuild
+constexpr unsigned kPSMax = 32768;    // largest P indexed by the sorted snapshot
 constexpr unsigned kHeavyFrontier = 512;  // frontiers this large are merged by a whole block
-constexpr unsigned kNodeSlots = 32;  // candidates a node holds in slots per step; more go to a list
-
-enum : uint8_t { ST_OPEN = 0, ST_CLOSED = 1, ST_DEAD = 2 };
+constexpr unsigned kHeavyCands = 32;      // ... and so are nodes reached by more candidates in a step
+constexpr unsigned kNodeSlots = 32;      // candidate slots per node and step in batch mode
+constexpr unsigned kNodeSlotsGrid = 128; // ... for a single query (whole-grid search)
 
 enum StatIdx {
   S_EXTRACTED = 0,
@@ -43,11 +54,18 @@ enum StatIdx {
   S_STEPS,
   S_FCMP,
   S_PCMP,
-  S_THIST,    // device ns spent in phase 1 (leader's view, barrier included)
-  S_TEXPAND,  // phase 2
-  S_TMERGE,   // phase 4
+  S_TSEL,     // device ns, leader's view: window selection and step control
+  S_TWORK,    // merge of window i overlapped with extraction + expansion of window i+1
+  S_TSYNC,    // end of step: histogram flush and grid barrier wait
   S_TOUT,     // output
   S_GOALINS,  // goal labels accepted into P during the search (P log length)
+  S_OSCAN,    // OPEN entries read by the extraction scans
+  S_OKEEP,    // OPEN entries copied to the next step's OPEN array
+  S_OVF,      // candidates beyond a node's slots (merged through the node's list)
+  S_MAXH,     // sum over steps of the longest heavy (block) merge of the step, ns
+  S_MAXL,     // ... of the longest light (warp) merge
+  S_MAXX,     // ... of the longest extraction work item
+  S_NHEAVY,   // heavy merges
   kNStat
 };
 
@@ -71,69 +89,102 @@ struct alignas(128) Hot {
   T v;
 };
 
-// Per-query control block (global memory). Counters that the team reads after
-// a barrier are plain words; concurrent updates use atomics.
+// Counters of one search step i, kept in a ring of three indexed by i % 3.
+// They are written during step i-1 (the OPEN array, window and candidates
+// step i works on are produced then) and read during step i; step i clears
+// the slot of step i+2.
+struct CycleCtl {
+  Hot<unsigned> open_count;         // entries of step i's OPEN array (FIFO: the ring's tail)
+  Hot<unsigned long long> min_key;  // smallest key among the entries carried over by extraction
+  Hot<unsigned> win_count;          // labels of window i
+  Hot<unsigned> win_min;            // smallest F[0] among them
+  Hot<unsigned> cand_count;         // candidates of window i (merged in step i)
+  Hot<unsigned> touched_count;      // nodes they reach with a small frontier (one warp each)
+  Hot<unsigned> heavy_count;        // ... with a large frontier (one block each)
+  Hot<unsigned> work_next;          // dynamic claims: index-rank items, light merges, extraction chunks
+  Hot<unsigned> heavy_next;         // dynamic claims of heavy merges
+  Hot<unsigned> f1lo;               // F[1] range of the carried entries in the split buckets
+  Hot<unsigned> f1hi;
+  Hot<unsigned> plen;               // P-log length every reader uses in step i
+  Hot<unsigned> lbase;              // labels that existed when step i began
+  unsigned win_min_prev;            // win_min of window i-1
+  unsigned head;                    // FIFO: the ring position window i+1 starts at (0 otherwise)
+  unsigned tmax[3];                 // longest heavy merge, light merge, extraction item of step i (ns)
+};
+
+// Bins of one OPEN array's histogram: F[0] origin, F[1] origin and shift of
+// the split buckets, F[0] bucket width.
+struct BinLimits {
+  uint32_t b0, b1, s1, delta;
+};
+
+// The P index as one step sees it (a pair indexed by step parity; step i
+// reads entry i & 1 and writes entry (i+1) & 1).
+struct PIdx {
+  unsigned cur, count, mark, ntiles;  // live buffer, entries (the log prefix [0, mark)), tiles
+  unsigned state;                     // rebuild in progress: 0 none, 1 rank, 2 scatter, 3 tiles
+  unsigned nb, k;                     // its target buffer and log prefix
+  unsigned shift[3];                  // per-objective shifts balancing the Z-order
+};
+
+// Per-query control block (global memory).
 struct QCtl {
   unsigned error;
   unsigned done;
   unsigned step;
-  unsigned theta;
-  unsigned plog_snap;
   unsigned res_count;
   unsigned res_status;
-  unsigned f1span[2];     // F[1] spread of the lowest F[0] bucket, measured per step
-  unsigned ps_cur, ps_count, ps_mark, ps_ntiles;   // live P index
-  unsigned ps_build, ps_src, ps_mark_new, ps_nbuild;
-  unsigned ps_shift[3];
-  unsigned ps_nb;         // index buffer being built this step
+  unsigned pad0;
   unsigned long long res_off;    // costs (count*d) then path offsets (count+1)
   unsigned long long res_path;   // nodes (total) then arc ids (total - count)
   unsigned long long res_total;  // total path nodes
   unsigned long long t_start;
   unsigned long long stats[kNStat];
+  PIdx pidx[2];
+  BinLimits bins[3];             // bins of step i's histogram at bins[i % 3]
+  CycleCtl cyc[3];
   Hot<unsigned> n_labels;
-  Hot<unsigned> open_count[2];
-  Hot<unsigned> win_count;
-  Hot<unsigned> cand_count;
-  Hot<unsigned> touched_count;
-  Hot<unsigned> merge_next;    // next touched node to merge (dynamic scheduling)
-  Hot<unsigned> heavy_count;   // touched nodes with a large frontier, merged by a whole block
-  Hot<unsigned> heavy_next;    // next heavy node to merge
-  Hot<unsigned> plog_len;
-  Hot<unsigned long long> min_key[2];  // lexicographic minimum (F0 << 32 | F1) of OPEN
+  Hot<unsigned> plog_len;        // the P log's length (written by the goal node's merge only)
+  Hot<unsigned> fifo_tail;       // FIFO: ring positions handed out so far
   Hot<unsigned long long> f_words;
   Hot<unsigned> bar_count;
   Hot<unsigned> bar_gen;
 };
 
-// Pointers into one query's arena (one slot).
-struct QArena {
-  uint64_t* fbase;     // n
-  uint32_t* fcount;    // n
-  uint32_t* fcap;      // n
-  int32_t* node_head;  // n: this step's candidates beyond the slots (linked by cnext)
-  uint32_t* ncand;     // n: candidates that reached the node this step
-  int32_t* cslot;      // n * kNodeSlots: the first kNodeSlots of them
-  uint32_t* lg;        // d * label_cap
-  uint32_t* lnode;
-  uint32_t* lparent;
-  uint32_t* ledge;
-  uint32_t* lpver;
-  uint8_t* lstatus;
-  uint32_t* fpool;
-  uint64_t* okey[2];   // OPEN keys (F0 << 32 | F1)
-  uint32_t* oid[2];    // OPEN label ids
-  uint32_t* ps[2];     // P index: d * plog_cap costs, Z-order
-  uint32_t* pst[2];    // P index tile minima: d * (plog_cap / 32 + 1)
-  uint32_t* window;
+// The candidates of one window, grouped by target node.
+struct CandSet {
+  uint32_t* ncand;     // n+1: candidates that reached the node
+  int32_t* cslot;      // (n+1) * nslots: the first nslots of them
+  int32_t* node_head;  // n+1: the rest, linked by cnext
+  uint32_t* hflag;     // n+1: the node is merged by a whole block (listed once among the heavy nodes)
   uint32_t* cnode;
   uint32_t* cparent;
   uint32_t* cedge;
   int32_t* cnext;
   uint32_t* cg;        // d * cand_cap
-  uint32_t* touched;
+  uint32_t* touched;   // 2 * cand_cap: every node reached from the front, block-merged ones from the back
+};
+
+// Pointers into one query's arena (one slot).
+struct QArena {
+  uint64_t* fbase;     // n+1
+  uint32_t* fcount;    // n+1
+  uint32_t* fcap;      // n+1
+  CandSet cs[2];
+  uint32_t* lg;        // d * label_cap
+  uint32_t* lnode;
+  uint32_t* lparent;
+  uint32_t* ledge;
+  uint32_t* lpver;     // P-log length at the label's last F-against-P test
+  uint32_t* ldead;     // step in which the label was pruned, kAlive if never
+  uint32_t* fpool;
+  uint64_t* okey[2];   // OPEN keys (F0 << 32 | F1)
+  uint32_t* oid[2];    // OPEN label ids
+  uint32_t* ps[2];     // P index: d * plog_cap costs, Z-order
+  uint32_t* pst[2];    // P index tile minima: d * (plog_cap / 32 + 1)
+  uint32_t* prank;     // kPSMax: ranks of a rebuild in progress
   uint32_t* plog;      // d * plog_cap
-  uint32_t* hist;      // 2 * kNB
+  uint32_t* hist;      // 3 * kNB (step i: hist + (i % 3) * kNB)
   uint32_t label_cap;
   uint32_t open_cap;
   uint32_t win_cap;
@@ -141,17 +192,21 @@ struct QArena {
   uint32_t plog_cap;
   uint32_t pad;
   unsigned long long fpool_words;
+  uint32_t nslots;     // candidate slots per node and step (the rest go to the node's list)
+  uint32_t pad2;
 };
 
 struct QParams {
   uint32_t start, goal;
-  const uint32_t* h;      // d * n
+  const uint32_t* h;      // qd * n (objective k of node v at h[k*n + v])
   uint32_t window;        // target W
   uint32_t lanes;         // lanes per label
   uint32_t delta;         // F[0] bucket width
   uint32_t tile;          // frontier growth granule
   uint32_t label_budget;  // max labels (<= label_cap)
   uint32_t flags;
+  uint32_t qd;            // objectives the query uses (<= the kernel's D; the rest read as 0)
+  uint32_t ps_grow;       // the P index is rebuilt once the log outgrows it by 32 + count >> ps_grow
   unsigned long long time_limit_ns;
 };
 

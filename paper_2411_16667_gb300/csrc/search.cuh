@@ -18,7 +18,7 @@ struct MSlot {     // one concurrent query: its arena and current parameters
   QParams P;
   GraphDev G;
   OutPool O;       // where its result goes (shared in batch mode, its own when serving)
-  unsigned d, state, qidx, pad;
+  unsigned d, state, qidx, pad;  // d: objectives the query uses (<= the kernel's)
 };
 
 struct MQuery {    // a queued query
@@ -51,13 +51,29 @@ struct QResult {
   unsigned long long stats[kNStat];
 };
 
+// Kernel launchers of one objective count D (search_inst.cu instantiates them,
+// one object per group of D values); the kernel of a query with qd < D
+// objectives reads objectives qd..D-1 as 0.
+template <int D>
+cudaError_t launch_grid(const GraphDev& G, const QArena& A, QCtl* C, const QParams& P, const OutPool& O,
+                        QResult* R, unsigned blocks, cudaStream_t s);
+template <int D>
+int grid_occupancy();
+template <int D>
+cudaError_t launch_multi_d(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue, unsigned* hctl,
+                           const GraphDev* graphs, QResult* results, unsigned* done_flags, MCtl* M, unsigned blocks,
+                           cudaStream_t s);
+template <int D>
+int multi_occupancy_d();
+
+// Dispatch on the objective count, 1..OPMOS_MAX_D (search_dispatch.cu).
 cudaError_t launch_search_grid(unsigned d, const GraphDev& G, const QArena& A, QCtl* C, const QParams& P,
                                const OutPool& O, QResult* R, unsigned blocks, cudaStream_t s);
-int search_occupancy(unsigned d, int batch);
-cudaError_t launch_multi(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue, unsigned* hctl,
-                         const GraphDev* graphs, QResult* results, unsigned* done_flags, MCtl* M,
+int search_occupancy(unsigned d);
+cudaError_t launch_multi(unsigned d, MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue,
+                         unsigned* hctl, const GraphDev* graphs, QResult* results, unsigned* done_flags, MCtl* M,
                          unsigned blocks, cudaStream_t s);
-int multi_occupancy();
+int multi_occupancy(unsigned d);
 
 // Ideal-point heuristic jobs: h_out[v] = shortest v->goal distance under
 // objective k (Sec. 4), one thread block per job.

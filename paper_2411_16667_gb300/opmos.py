@@ -18,8 +18,10 @@ _lib = None
 OK, ERR_INVALID_ARG, ERR_OVERFLOW, ERR_OUT_OF_MEMORY, ERR_CAPACITY, ERR_BUDGET, ERR_TIMEOUT, ERR_CUDA, PENDING = range(9)
 FLAG_NO_PATHS = 1
 FLAG_GRAPH = 2
-MAX_D = 8
+FLAG_FIFO = 4
+MAX_D = 16
 
+TEST_EXPORTS = ("opmos_test_merge", "opmos_test_window")  # include/opmos_test.h
 EXPORTS = ("opmos_default_options", "opmos_device_count", "opmos_graph_create", "opmos_graph_destroy",
            "opmos_heuristic", "opmos_heuristic_copy", "opmos_heuristic_destroy", "opmos_solve",
            "opmos_solve_batch", "opmos_result_count", "opmos_result_d", "opmos_result_costs",
@@ -45,11 +47,16 @@ class Stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in (
         "extracted", "dead_skipped", "goal_pruned", "candidates", "inserted", "pruned", "steps",
         "frontier_cmp", "p_cmp", "bytes", "heuristic_ns", "search_ns", "total_ns")] + [
-        ("phase_ns", ctypes.c_uint64 * 4), ("goal_inserted", ctypes.c_uint64)]
+        ("phase_ns", ctypes.c_uint64 * 4), ("goal_inserted", ctypes.c_uint64),
+        ("open_scanned", ctypes.c_uint64), ("open_rewritten", ctypes.c_uint64),
+        ("list_candidates", ctypes.c_uint64), ("longest_task_ns", ctypes.c_uint64 * 3),
+        ("heavy_merges", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
-        d = {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "phase_ns"}
-        d["phase_ns"] = [int(x) for x in self.phase_ns]
+        arrays = ("phase_ns", "longest_task_ns")
+        d = {f: int(getattr(self, f)) for f, _ in self._fields_ if f not in arrays}
+        for f in arrays:
+            d[f] = [int(x) for x in getattr(self, f)]
         return d
 
 
@@ -91,6 +98,8 @@ def lib(path: str | None = None):
         L.opmos_server_destroy.restype = None
         L.opmos_last_error.restype = ctypes.c_char_p
         L.opmos_heuristic_noalloc.argtypes = [vp, u32, u32, vp, vp]
+        L.opmos_test_merge.argtypes = [u32, u32, vp, u32, vp, vp, u32, u32, vp, vp, ctypes.POINTER(u32)]
+        L.opmos_test_window.argtypes = [u32, vp, vp, vp, u32, vp, vp, ctypes.POINTER(u32)]
         _lib = L
     return _lib
 
@@ -289,3 +298,39 @@ class opmos_server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# test hooks (include/opmos_test.h): single device routines on given inputs
+# ---------------------------------------------------------------------------
+def opmos_test_merge(front, cand, cand_arc, block: bool, slots: int = 32):
+    """Device merge of one node (frontier rows ``front``, candidate rows
+    ``cand`` with arc ids ``cand_arc``); returns (costs, origins) of the
+    frontier after the merge (origin < len(front): that entry; else
+    len(front) + candidate index)."""
+    front = np.ascontiguousarray(front, np.uint32)
+    cand = np.ascontiguousarray(cand, np.uint32)
+    arc = np.ascontiguousarray(cand_arc, np.uint32)
+    d = int(front.shape[1] if front.size else cand.shape[1])
+    nf, nc = int(front.shape[0]), int(cand.shape[0])
+    out = np.zeros((nf + nc + 1, d), np.uint32)
+    org = np.zeros(nf + nc + 1, np.uint32)
+    cnt = ctypes.c_uint32()
+    _check(lib().opmos_test_merge(d, nf, _ptr(front), nc, _ptr(cand), _ptr(arc), int(block), slots, _ptr(out),
+                                  _ptr(org), ctypes.byref(cnt)), "opmos_test_merge")
+    return out[:cnt.value], org[:cnt.value]
+
+
+def opmos_test_window(f0, f1, dead, window: int, bins):
+    """Device window selection and extraction over OPEN entries with
+    F = (f0, f1); returns (taken bool array, b*)."""
+    f0 = np.ascontiguousarray(f0, np.uint32)
+    f1 = np.ascontiguousarray(f1, np.uint32)
+    dead = np.ascontiguousarray(dead, np.uint8)
+    bins = np.ascontiguousarray(bins, np.uint32)
+    n = int(f0.shape[0])
+    taken = np.zeros(max(n, 1), np.uint8)
+    bstar = ctypes.c_uint32()
+    _check(lib().opmos_test_window(n, _ptr(f0), _ptr(f1), _ptr(dead), window, _ptr(bins), _ptr(taken),
+                                   ctypes.byref(bstar)), "opmos_test_window")
+    return taken[:n].astype(bool), int(bstar.value)

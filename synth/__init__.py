@@ -23,6 +23,9 @@ scaled up; the TMPLAR/ERA5 graphs themselves are not available):
   256 queries with hop distance U[50,400].
 * ``config4``  the config-2 grid plus an exposure field and a step count,
   d=5; 1,024 queries with Chebyshev distance U[16,128].
+* ``time_route`` a time-expanded ship route (cells x time windows, two
+  speeds per move) with up to 12 objectives in the order of Table 1, for the
+  high objective counts of the paper's routes (Sec. 6.1, Tables 1-2).
 * ``random_digraph`` / ``small_grid``: tiny graphs with ties and zero costs.
 """
 from __future__ import annotations
@@ -356,6 +359,117 @@ def config3(seed: int = 1, nq: int = 256, npts: int = 200_000) -> tuple[Graph, l
         t = int(cand[rand_int(seed, 522, ctr, 0, cand.size - 1)])
         queries.append((s, t))
     return g, queries
+
+
+# --------------------------------------------------------------------------
+# Time-expanded ship routes (high objective counts)
+# --------------------------------------------------------------------------
+ROUTE_OBJECTIVES = ("distance", "fuel", "roll", "pitch", "vertical acceleration", "horizontal acceleration",
+                    "vertical bending moment", "vertical shear force", "wave height", "wave period",
+                    "relative wave bearing", "random")
+
+
+def _drifting_field(seed: int, stream: int, rows: int, cols: int, windows: int, nblobs: int = 6) -> np.ndarray:
+    """A smooth field per time window: ``nblobs`` Gaussian blobs (sigma
+    U[1.5, 4] cells, amplitude U[0.5, 1]) whose centres drift by a fixed
+    seeded velocity (up to 0.6 cells per window); min-max normalised to [0, 1]
+    over all windows. Shape [windows, rows, cols]."""
+    i = np.arange(nblobs)
+    cy = rand_unit(seed, stream, 6 * i) * rows
+    cx = rand_unit(seed, stream, 6 * i + 1) * cols
+    vy = (rand_unit(seed, stream, 6 * i + 2) - 0.5) * 1.2
+    vx = (rand_unit(seed, stream, 6 * i + 3) - 0.5) * 1.2
+    sig = 1.5 + 2.5 * rand_unit(seed, stream, 6 * i + 4)
+    amp = 0.5 + 0.5 * rand_unit(seed, stream, 6 * i + 5)
+    y = np.arange(rows, dtype=np.float64)[None, :, None]
+    x = np.arange(cols, dtype=np.float64)[None, None, :]
+    w = np.arange(windows, dtype=np.float64)[:, None, None]
+    f = np.zeros((windows, rows, cols))
+    for b in range(nblobs):
+        f += amp[b] * np.exp(-((y - cy[b] - vy[b] * w) ** 2 + (x - cx[b] - vx[b] * w) ** 2) / (2.0 * sig[b] ** 2))
+    lo, hi = f.min(), f.max()
+    return (f - lo) / (hi - lo) if hi > lo else np.zeros_like(f)
+
+
+def time_route(seed: int, rows: int, cols: int, windows: int = 10, d: int = 12) -> tuple[Graph, list[tuple[int, int]]]:
+    """A time-expanded ship route shaped like the paper's TMPLAR graphs
+    (Sec. 6.1: a reduced corridor, each location expanded into time windows,
+    up to 12 objectives used in the order of Table 1), from seeded drifting
+    weather fields instead of ERA5 data.
+
+    Nodes: (cell, window) for the rows x cols 8-connected cells and
+    ``windows`` time windows, id = cell * windows + window, plus one goal node
+    (id rows*cols*windows) that every window of the destination cell reaches
+    at zero cost. A move to a neighbouring cell departs in window w and
+    arrives in window w+1 (fast, speed 3), w+2 (speed 2) or w+3 (slow, speed
+    1); moves past the last window do not exist. Start: cell (0, 0) in window 0; destination: cell
+    (rows-1, cols-1).
+
+    Objectives of a move (integers, all >= 0), from seven wave-height
+    components h0..h6, the wave period p and the wave direction (fields at
+    the move's midpoint in its departure window, each in [0, 1]), the
+    relative bearing b in [0, 1] (0 following seas, 1 head seas), the move
+    length L (10 straight, 14 diagonal) and the speed s (1, 2 or 3):
+      distance L; fuel round(L (s + 2h0)); roll round(L (1 + 8h1 sin(pi b)));
+      pitch round(L (1 + 8h2 b)); vertical acceleration round(L (1 + 4h3 b s^2));
+      horizontal acceleration round(L (1 + 4h4 sin(pi b) s)); vertical
+      bending moment round(L (1 + 6h5 p)); vertical shear force
+      round(L (1 + 6h6 (1 - p))); wave height round(L/10 (10 + 70h0)); wave
+      period round(L/10 (10 + 70p)); relative wave bearing round(8Lb);
+      random U[1, 100] per arc."""
+    assert 1 <= d <= len(ROUTE_OBJECTIVES) and rows >= 1 and cols >= 1 and windows >= 2
+    # seven wave-height components (one per response objective), the period
+    # and the direction
+    HS = [_drifting_field(seed, 1220 + j, rows, cols, windows) for j in range(7)]
+    Pd = _drifting_field(seed, 1201, rows, cols, windows)
+    TH = _drifting_field(seed, 1202, rows, cols, windows) * (2.0 * np.pi)
+    csrc, cdst, diag = grid8_arcs(rows, cols)
+    ncell = rows * cols
+    goal = ncell * windows
+    n = goal + 1
+    srcs, dsts, objs = [], [], []
+    length = np.where(diag, 14, 10).astype(np.float64)
+    r0, c0 = csrc // cols, csrc % cols
+    r1, c1 = cdst // cols, cdst % cols
+    bearing = np.arctan2(r1 - r0, c1 - c0)
+    for speed, tau in ((3, 1), (2, 2), (1, 3)):
+        for w in range(windows - tau):
+            hs = [0.5 * (f[w].reshape(-1)[csrc] + f[w].reshape(-1)[cdst]) for f in HS]
+            pf, tf = Pd[w].reshape(-1), TH[w].reshape(-1)
+            p = 0.5 * (pf[csrc] + pf[cdst])
+            th = 0.5 * (tf[csrc] + tf[cdst])
+            rel = np.abs(np.angle(np.exp(1j * (bearing - th)))) / np.pi  # 0 following, 1 head seas
+            L10 = length / 10.0
+            sb = np.sin(np.pi * rel)
+            idx = np.arange(csrc.shape[0]) + csrc.shape[0] * (w + windows * (speed - 1))
+            o = [length,
+                 length * (speed + 2.0 * hs[0]),
+                 length * (1.0 + 8.0 * hs[1] * sb),
+                 length * (1.0 + 8.0 * hs[2] * rel),
+                 length * (1.0 + 4.0 * hs[3] * rel * speed * speed),
+                 length * (1.0 + 4.0 * hs[4] * sb * speed),
+                 length * (1.0 + 6.0 * hs[5] * p),
+                 length * (1.0 + 6.0 * hs[6] * (1.0 - p)),
+                 L10 * (10.0 + 70.0 * hs[0]),
+                 L10 * (10.0 + 70.0 * p),
+                 L10 * 80.0 * rel,
+                 rand_int(seed, 1210, idx, 1, 100).astype(np.float64)]
+            srcs.append(csrc * windows + w)
+            dsts.append(cdst * windows + w + tau)
+            objs.append(np.floor(np.stack(o[:d]) + 0.5).astype(np.int64))
+    dest = ncell - 1
+    sink_src = dest * windows + np.arange(windows)
+    srcs.append(sink_src)
+    dsts.append(np.full(windows, goal))
+    objs.append(np.zeros((d, windows), np.int64))
+    src = np.concatenate(srcs)
+    dst = np.concatenate(dsts)
+    cost = np.concatenate(objs, axis=1)
+    rowptr, col, cost = _csr_from_arcs(n, src, dst, cost)
+    g = Graph(f"route{rows}x{cols}x{windows}-d{d}-s{seed}", n, d, rowptr, col, cost,
+              {"rows": rows, "cols": cols, "windows": windows, "seed": seed,
+               "objectives": ROUTE_OBJECTIVES[:d]})
+    return g, [(0, goal)]
 
 
 # --------------------------------------------------------------------------

@@ -4,6 +4,7 @@ Usage: python tests/golden/make_golden.py config2 [--seed 1]
        python tests/golden/make_golden.py config4 --digests --jobs 6
        python tests/golden/make_golden.py config3 --digests --shortest-hops 8 \
               --budget 5000000 --jobs 8
+       python tests/golden/make_golden.py routes --jobs 4
 
 Only the oracle (Algorithm 1, ``oracle/``) and the input generators
 (``synth``) are called. Each fixture records the graph digest so a test can
@@ -22,7 +23,11 @@ Digest format (``--digests``; one line per query of the config):
     <qi> <start> <goal> <count> <labels> <extracted> <sha256 of the sorted
     front as little-endian uint32, first 16 hex digits>
 A query the oracle cannot finish within ``--budget`` labels is written with
-count -1. ``--shortest-hops K`` restricts the digests to the K queries with
+count -1.
+
+Route digests (``routes``; time-expanded ship routes of ``synth.time_route``,
+one line per instance in ROUTES):
+    <name> <graph digest> <start> <goal> <count> <labels> <extracted> <sha256[:16]> ``--shortest-hops K`` restricts the digests to the K queries with
 the fewest hops between start and goal (breadth-first search, ties by query
 index): the queries most likely to finish at full d.
 """
@@ -123,9 +128,39 @@ def write_digests(args):
     print(path, len(lines), "queries")
 
 
+# time-expanded routes with oracle digests: (seed, rows, cols, windows, d)
+ROUTES = [(1, 4, 6, 20, 12), (1, 6, 8, 24, 8), (1, 6, 8, 24, 10), (1, 6, 8, 24, 12)]
+
+
+def _route_job(spec):
+    seed, rows, cols, windows, d = spec
+    g, q = synth.time_route(seed, rows, cols, windows, d)
+    s, t = q[0]
+    t0 = time.time()
+    f = oracle.solve(g, s, t)
+    print(f"{g.name}: {len(f.costs)} solutions, {f.stats['extracted']} extracted, {time.time() - t0:.1f}s",
+          flush=True)
+    return (f"{g.name} {g.digest()} {s} {t} {len(f.costs)} {f.stats['labels']} {f.stats['extracted']} "
+            f"{front_digest(f.costs)}")
+
+
+def write_routes(args):
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(args.jobs) as pool:
+        lines = pool.map(_route_job, ROUTES)
+    path = os.path.join(HERE, "routes.digests")
+    with open(path + ".tmp", "w") as f:
+        f.write("# oracle fronts (Algorithm 1) of time-expanded ship routes (synth.time_route) as digests\n")
+        f.write("# name graph-digest start goal count labels extracted sha256[:16]\n")
+        for line in lines:
+            f.write(line + "\n")
+    os.replace(path + ".tmp", path)
+    print(path, len(lines), "routes")
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("config", choices=["config1", "config2", "config3", "config4"])
+    ap.add_argument("config", choices=["config1", "config2", "config3", "config4", "routes"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--queries", default="0:1", help="slice lo:hi of the config's query list")
     ap.add_argument("--d", type=int, default=0, help="use only the first d objectives")
@@ -134,6 +169,9 @@ def main():
     ap.add_argument("--budget", type=int, default=0, help="oracle label budget per query")
     ap.add_argument("--shortest-hops", type=int, default=0, help="digests of the K fewest-hop queries only")
     args = ap.parse_args()
+    if args.config == "routes":
+        write_routes(args)
+        return
     if args.digests:
         write_digests(args)
         return

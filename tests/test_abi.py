@@ -18,8 +18,20 @@ def _declared_symbols():
     return sorted(set(re.findall(r"OPMOS_API\s+[\w\s\*]+?\b(opmos_\w+)\(", text)))
 
 
+def _declared_test_symbols():
+    text = open(os.path.join(ROOT, "include", "opmos_test.h")).read()
+    return sorted(set(re.findall(r"OPMOS_API\s+[\w\s\*]+?\b(opmos_\w+)\(", text)))
+
+
 def test_header_declares_the_binding_exports():
     assert _declared_symbols() == sorted(opmos.EXPORTS)
+    assert _declared_test_symbols() == sorted(opmos.TEST_EXPORTS)
+
+
+def test_library_exports_the_test_hooks():
+    lib = ctypes.CDLL(pkg.build())
+    for name in _declared_test_symbols():
+        assert hasattr(lib, name), name
 
 
 def test_library_builds_and_exports_every_symbol():
@@ -34,7 +46,7 @@ def test_options_struct_matches_defaults():
     assert (o.window, o.lanes_per_label, o.tile, o.delta) == (1024, 8, 32, 1)
     assert o.mem_budget_bytes == 8 << 30
     assert ctypes.sizeof(opmos.Options) == 48
-    assert ctypes.sizeof(opmos.Stats) == 18 * 8
+    assert ctypes.sizeof(opmos.Stats) == 25 * 8
 
 
 @pytest.mark.skipif(opmos.opmos_device_count() > 0, reason="only meaningful without a GPU")

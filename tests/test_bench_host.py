@@ -52,3 +52,12 @@ def test_oracle_count_bytes_of_the_headline_query():
               + 4 * (fx["pruned_open"] + fx["pruned_open_goal"] + fx["pruned_closed"] + fx["pruned_p"]))
     assert bench.oracle_count_bytes(fx, d) == expect
     assert 7.0e11 < expect < 7.5e11
+
+
+def test_grid_distance_estimates_query_cost():
+    import bench
+    import synth
+    g, _ = synth.config1()
+    assert bench.grid_distance(g, [(0, 1023), (0, 33), (5, 5)]) == [31, 1, 0]
+    r, _ = synth.time_route(1, 3, 4, 6, 2)
+    assert bench.grid_distance(r, [(0, r.n - 1)]) == [1]

@@ -262,15 +262,41 @@ def test_batch_matches_oracle_on_small_ship_queries(op):
         check_front(g, s, t, res.costs, res.paths)
 
 
+def _same_paths(a, b):
+    assert len(a.paths) == len(b.paths)
+    for (na, ea), (nb, eb) in zip(a.paths, b.paths):
+        assert np.array_equal(na, nb) and np.array_equal(ea, eb)
+
+
 def test_batch_equals_single(op):
-    """Each query's front is the same alone and in the batch."""
+    """Each query's result -- front and the path kept for every cost -- is
+    the same alone and in the batch, given the same launch parameters (ties
+    between equal-cost candidates go to the smallest arc id; a label pruned
+    in a step is still extractable in it, so the windows do not depend on
+    thread timing)."""
     g, queries = synth.config4(2, nq=12)
     G = op.opmos_graph.from_synth(g)
     out = op.opmos_solve_batch(G, [s for s, _ in queries], [t for _, t in queries], window=64)
     for (s, t), (st, res) in zip(queries, out):
         assert st == op.OK
-        alone = op.opmos_solve(G, s, t)
+        alone = op.opmos_solve(G, s, t, window=64)
         assert np.array_equal(res.costs, alone.costs)
+        _same_paths(res, alone)
+        check_front(g, s, t, res.costs, res.paths)
+
+
+def test_paths_repeat_exactly(op):
+    """Three runs of the same query, single and batched, keep the same path
+    for every cost (SURVEY reading c5: several paths may carry one cost; the
+    library's choice is deterministic)."""
+    g, q = synth.ship_grid(9, 96, 3)
+    s, t = q[0]
+    G = op.opmos_graph.from_synth(g)
+    runs = [op.opmos_solve(G, s, t, window=256) for _ in range(3)]
+    runs += [op.opmos_solve_batch(G, [s, 0], [t, 5000], window=256)[0][1]]
+    for r in runs[1:]:
+        assert np.array_equal(r.costs, runs[0].costs)
+        _same_paths(r, runs[0])
 
 
 def test_batch_graph_capture_gives_the_same_fronts(op):
@@ -365,3 +391,38 @@ def test_config3_full_d_batch_under_label_budget(op):
         assert st in (op.OK, op.ERR_BUDGET), f"query {s}->{t} status {st}"
         if st == op.OK:
             check_front_sampled(g, s, t, res.costs, res.paths)
+
+
+# ---------------------------------------------------------------------------
+# FIFO (relaxed-order) OPEN: Sec. 4 and 7.1 compare it with the priority queue
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("window", [1, 64, 1024])
+def test_fifo_order_gives_the_same_front(op, window):
+    """OPMOS_FLAG_FIFO takes the oldest OPEN entries each step instead of the
+    lexicographically lowest: the front is the same, only the work differs."""
+    cases = [synth.config1(), synth.ship_grid(3, 48, 3), (synth.random_digraph(5, 9, 4, p=0.35, cmax=3), [(0, 8)])]
+    for g, q in cases:
+        s, t = q[0]
+        G = op.opmos_graph.from_synth(g)
+        exp = oracle.solve(g, s, t)
+        res = op.opmos_solve(G, s, t, window=window, flags=op.FLAG_FIFO)
+        _same_front(res, exp.costs)
+        check_front(g, s, t, res.costs, res.paths)
+
+
+def test_fifo_batch_and_work_ratio(op):
+    """FIFO in a batch launch gives the oracle's fronts; on the 48x48 ship
+    grid it extracts more labels than the ordered window of the same width
+    (the work inefficiency of Sec. 4)."""
+    g, queries = synth.config4(2, nq=12)
+    G = op.opmos_graph.from_synth(g)
+    starts, goals = [s for s, _ in queries], [t for _, t in queries]
+    out = op.opmos_solve_batch(G, starts, goals, window=256, flags=op.FLAG_FIFO)
+    for (s, t), (st, res) in zip(queries, out):
+        assert st == op.OK
+        _same_front(res, op.opmos_solve(G, s, t, window=256).costs)
+    g2, q2 = synth.ship_grid(3, 48, 3)
+    G2 = op.opmos_graph.from_synth(g2)
+    ordered = op.opmos_solve(G2, *q2[0], window=256)
+    fifo = op.opmos_solve(G2, *q2[0], window=256, flags=op.FLAG_FIFO)
+    assert fifo.stats["extracted"] > ordered.stats["extracted"]

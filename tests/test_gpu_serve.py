@@ -57,7 +57,7 @@ def test_server_mixed_graphs_and_objective_counts(op):
         plan.append((gi, d, s, t))
     # each query alone, before the server makes its kernel resident (other
     # compute entry points must not run beside a resident server kernel)
-    alone = [op.opmos_solve(G[gi], s, t, d_used=d).costs for gi, d, s, t in plan]
+    alone = [op.opmos_solve(G[gi], s, t, d_used=d, window=64) for gi, d, s, t in plan]
     srv = op.opmos_server(G, mem_budget_bytes=8 << 30, window=64)
     first = [srv.submit(*p) for p in plan[:18]]
     time.sleep(0.01)  # the rest arrives while the first ones run
@@ -68,7 +68,10 @@ def test_server_mixed_graphs_and_objective_counts(op):
         st, r = results[ticket]
         assert st == op.OK, f"query {(gi, d, s, t)} status {st}"
         gd = graphs[gi].first_objectives(d)
-        assert np.array_equal(r.costs, ref)
+        assert np.array_equal(r.costs, ref.costs)
+        assert len(r.paths) == len(ref.paths)
+        for (na, ea), (nb, eb) in zip(r.paths, ref.paths):  # the same path for every cost
+            assert np.array_equal(na, nb) and np.array_equal(ea, eb)
         assert np.array_equal(r.costs, oracle.solve(gd, s, t).costs)
         check_front(gd, s, t, r.costs, r.paths)
 

@@ -26,10 +26,12 @@ def _worker(rank, world, port, out_dir):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         mine = bench.shard_queries(10, rank, world)
+        est = [5, 1, 9, 9, 2, 7, 3, 3, 8, 0]
+        by_cost = bench.shard_queries(10, rank, world, est)
         m = bench.max_over_ranks(float(10 * (rank + 1)), device="cpu")
         bench.barrier()
         with open(os.path.join(out_dir, f"r{rank}.json"), "w") as f:
-            json.dump({"mine": mine, "max": m}, f)
+            json.dump({"mine": mine, "max": m, "by_cost": by_cost}, f)
     finally:
         dist.destroy_process_group()
 
@@ -43,6 +45,13 @@ def test_shards_are_disjoint_and_max_is_global(tmp_path):
     assert allq == list(range(10))
     assert not set(res[0]["mine"]) & set(res[1]["mine"])
     assert all(r["max"] == 20.0 for r in res)
+    # by estimated cost: disjoint, complete, and the two ranks' totals within the largest single cost
+    est = [5, 1, 9, 9, 2, 7, 3, 3, 8, 0]
+    assert sorted(q for r in res for q in r["by_cost"]) == list(range(10))
+    tot = [sum(est[i] for i in r["by_cost"]) for r in res]
+    assert abs(tot[0] - tot[1]) <= max(est)
+    assert {2, 3} <= set(res[0]["by_cost"]) | set(res[1]["by_cost"])
+    assert not ({2, 3} <= set(res[0]["by_cost"])), "the two most expensive queries go to different ranks"
 
 
 def test_single_process_helpers_without_a_group():

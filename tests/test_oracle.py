@@ -60,15 +60,29 @@ def test_brute_force_random_digraphs(seed):
     check_front(g, s, t, res.costs, res.paths)
 
 
-@pytest.mark.parametrize("d,seed", [(d, seed) for d in (6, 7, 8) for seed in (301, 304, 306, 308)])
+@pytest.mark.parametrize("d,seed", [(d, seed) for d in range(6, 17) for seed in (301, 304, 306, 308)])
 def test_brute_force_high_d(d, seed):
-    """The same pin at d = 6..8, the objective counts up to the library's
-    maximum (8-node graphs whose fronts hold 6 to 12 vectors)."""
+    """The same pin at d = 6..16, the objective counts up to the library's
+    maximum (8-node graphs whose fronts hold 6 to 14 vectors)."""
     n = 8
     g = synth.random_digraph(seed, n, d, p=0.45, cmax=3)
     s, t = 0, n - 1
     res = oracle.solve(g, s, t)
     assert _tuples(res.costs) == brute_front(g, s, t)
+    check_front(g, s, t, res.costs, res.paths)
+
+
+@pytest.mark.parametrize("rows,cols,windows,d", [(2, 3, 6, 8), (2, 4, 6, 10), (3, 3, 6, 12), (2, 4, 6, 12),
+                                                  (3, 3, 5, 9)])
+def test_brute_force_time_routes(rows, cols, windows, d):
+    """Brute force on tiny time-expanded ship routes at high d (the routes
+    of Sec. 6.1 run up to 12 objectives); the goal is reached through
+    zero-cost arcs from every time window of the destination cell."""
+    g, q = synth.time_route(3, rows, cols, windows, d)
+    s, t = q[0]
+    res = oracle.solve(g, s, t)
+    assert _tuples(res.costs) == brute_front(g, s, t)
+    assert len(res.costs) >= 6
     check_front(g, s, t, res.costs, res.paths)
 
 

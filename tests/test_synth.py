@@ -125,3 +125,46 @@ def test_config3_query_hops(road):
     g, q = road
     for s, t in q[:8]:
         assert 50 <= _hops(g, s, t) <= 400
+
+
+def test_time_route_recipe():
+    """Time-expanded route: (cell, window) nodes plus a goal node; a move
+    arrives 1, 2 or 3 windows after it departs (speeds 3, 2, 1); the goal is
+    entered from every window of the destination cell at zero cost; the first
+    objectives keep the order of Table 1 and the stated ranges."""
+    rows, cols, w, d = 3, 4, 8, 12
+    g, q = synth.time_route(1, rows, cols, w, d)
+    ncell = rows * cols
+    goal = ncell * w
+    assert (g.n, g.d) == (goal + 1, 12) and q == [(0, goal)]
+    assert g.meta["objectives"][:2] == ("distance", "fuel") and g.meta["objectives"][-1] == "random"
+    src, dst = _arcs(g)
+    into_goal = dst == goal
+    assert np.array_equal(np.sort(src[into_goal]), (ncell - 1) * w + np.arange(w))
+    assert np.all(g.cost[:, into_goal] == 0)
+    assert np.diff(g.rowptr.astype(np.int64))[goal] == 0, "the goal has no out-arcs"
+    mv = ~into_goal
+    cu, wu = np.divmod(src[mv], w)
+    cv, wv = np.divmod(dst[mv], w)
+    tau = wv - wu
+    assert set(np.unique(tau)) == {1, 2, 3}
+    ru, cu_ = np.divmod(cu, cols)
+    rv, cv_ = np.divmod(cv, cols)
+    cheb = np.maximum(np.abs(ru - rv), np.abs(cu_ - cv_))
+    assert np.all(cheb == 1), "moves go to one of the 8 neighbouring cells"
+    diag = (ru != rv) & (cu_ != cv_)
+    c = g.cost[:, mv].astype(np.int64)
+    assert np.array_equal(c[0], np.where(diag, 14, 10)), "distance is the move length"
+    speed = 4 - tau
+    L = c[0]
+    assert np.all(c[1] >= L * speed) and np.all(c[1] <= L * (speed + 2) + 1), "fuel = L (s + 2 h0)"
+    for k in range(2, 8):
+        assert np.all(c[k] >= L) and np.all(c[k] <= 49 * L // 10 * 10 + 14 * 8 * 9), k
+    assert c[10].min() >= 0 and c[10].max() <= 8 * 14
+    assert c[11].min() >= 1 and c[11].max() <= 100, "random objective U[1, 100]"
+    # a seeded pure function; fewer objectives are a prefix of more
+    g2, _ = synth.time_route(1, rows, cols, w, d)
+    assert g2.digest() == g.digest()
+    g8, _ = synth.time_route(1, rows, cols, w, 8)
+    assert np.array_equal(g8.cost, g.cost[:8]) and np.array_equal(g8.col, g.col)
+    assert synth.time_route(2, rows, cols, w, d)[0].digest() != g.digest()
