@@ -402,8 +402,11 @@ struct Search {
     // a whole block; its light item then only clears hflag. Only light items
     // touch hflag during the merge, so a block merge never races a warp.
     if (pos == 0) cs.touched[agg_inc(&K1.touched_count.v)] = v2;
-    const bool big = pos == 0 && v2 != G.n && A.fcount[v2] >= kHeavyFrontier;
-    if ((big || (pos == kHeavyCands && v2 != G.n)) && atomicExch(&cs.hflag[v2], 1u) == 0u)
+    // (the work of a one-warp merge grows with frontier x candidates)
+    const bool heavy = v2 != G.n && ((pos == 0 && A.fcount[v2] >= kHeavyFrontier) ||
+                                     (pos == kHeavyCands / 2 - 1 && A.fcount[v2] >= kHeavyFrontier * 3 / 8) ||
+                                     pos == kHeavyCands);
+    if (heavy && atomicExch(&cs.hflag[v2], 1u) == 0u)
       cs.touched[2u * A.cand_cap - 1u - atomicAdd(&K1.heavy_count.v, 1u)] = v2;
   }
 
@@ -448,11 +451,14 @@ struct Search {
   }
 
   // ---------------- extraction of window i+1 from OPEN_i ----------------
-  // One warp, kChunk entries, 32 at a time: dead entries are dropped (lazy
-  // OPEN delete), window entries whose F a logged solution weakly dominates
-  // are dropped (lazy PruneOPEN), the other window entries are taken and
-  // expanded at once by lane groups; every other entry is carried to
-  // OPEN_{i+1} and counted in its histogram.
+  // One warp, the kChunk entries chunk, chunk + nchunks, chunk + 2 nchunks,
+  // ... (a merge appends a node's new labels side by side and they tend to
+  // fall in the same window, so strided chunks spread the window's labels
+  // over the work items): dead entries are dropped (lazy OPEN delete), window
+  // entries whose F a logged solution weakly dominates are dropped (lazy
+  // PruneOPEN), the other window entries are taken and expanded at once by
+  // lane groups; every other entry is carried to OPEN_{i+1} and counted in
+  // its histogram.
   __device__ void extract_chunk(unsigned chunk, unsigned n_in, const BinParams& bp, CycleCtl& K1) {
     const unsigned cur = cyc & 1u, nxt = cur ^ 1u;
     const uint64_t* in = A.okey[cur];
@@ -466,10 +472,10 @@ struct Search {
     const unsigned L = P.lanes, G_per = 32 / L, grp = lane / L, gl = lane % L;
     unsigned long long kmin = ~0ull, pcmp = 0;
     unsigned wmin = kInf, f1lo = kInf, f1hi = 0;
-    const unsigned end = min(n_in, (chunk + 1) * kChunk);
-    for (unsigned base = chunk * kChunk; base < end; base += 32) {
-      const unsigned i = base + lane;
-      const bool valid = i < end;
+    const unsigned nchunks = (n_in + kChunk - 1) / kChunk;
+    for (unsigned r = 0; r < kChunk; r += 32) {
+      const unsigned i = chunk + (r + lane) * nchunks;
+      const bool valid = i < n_in;
       uint64_t key = 0;
       uint32_t id = 0;
       bool keep = false, want = false;
