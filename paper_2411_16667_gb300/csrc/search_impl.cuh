@@ -181,6 +181,7 @@ struct Search {
   // frontier tiles loaded per round of a scan: fewer at high d (registers)
   static constexpr int kU = D <= 4 ? 4 : (D <= 8 ? 2 : 1);
   static constexpr int kUH = D <= 8 ? 2 : 1;
+  static constexpr int kPT = D <= 4 ? 4 : (D <= 8 ? 2 : 1);  // P-index tiles loaded per round
 
   const GraphDev& G;
   const QArena& A;
@@ -694,15 +695,27 @@ struct Search {
             cnt += min(32u, tg_hi - tg);
             bool dead = false;
             while (pm && !dead) {
-              const unsigned tt = __ffs(pm) - 1;
-              pm &= pm - 1;
-              const unsigned e = (tg + tt) * 32 + lane;
-              const bool ve = e < pcount;
-              uint32_t p[D];
+              // up to kPT passing tiles per round: their loads overlap
+              unsigned tt[kPT];
 #pragma unroll
-              for (int k = 0; k < D; ++k) p[k] = ve ? ps[(size_t)k * A.plog_cap + e] : kInf;
-              dead = __ballot_sync(0xffffffffu, ve && weakly_le<D>(p, Fj)) != 0;
-              cnt += 32;
+              for (int q = 0; q < kPT; ++q) {
+                tt[q] = pm ? __ffs(pm) - 1 : 32u;
+                pm &= pm - 1;
+              }
+              uint32_t p[kPT][D];
+              bool ve[kPT];
+#pragma unroll
+              for (int q = 0; q < kPT; ++q) {
+                const unsigned e = (tg + tt[q]) * 32 + lane;
+                ve[q] = tt[q] < 32u && e < pcount;
+#pragma unroll
+                for (int k = 0; k < D; ++k) p[q][k] = ve[q] ? ps[(size_t)k * A.plog_cap + e] : kInf;
+              }
+#pragma unroll
+              for (int q = 0; q < kPT; ++q) {
+                dead |= __ballot_sync(0xffffffffu, ve[q] && weakly_le<D>(p[q], Fj)) != 0;
+                cnt += tt[q] < 32u ? 32 : 0;
+              }
             }
             if (dead && lane == j) alive = false;
           }
