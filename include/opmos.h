@@ -223,8 +223,9 @@ OPMOS_API void opmos_result_free(opmos_result* r);
 
 /* Continuous-batching server over device-resident graphs. Queries submitted
  * while others run are admitted as soon as a slot and the device memory
- * budget (opt->mem_budget_bytes, default 64 GiB; one slot = a 512 MiB search
- * arena + a 32 MiB result pool) allow; admitted queries run concurrently in
+ * budget (opt->mem_budget_bytes, default 64 GiB; one slot = a search arena of
+ * 512 MiB, or of what opt->label_budget labels need when that is more, + a
+ * 32 MiB result pool) allow; admitted queries run concurrently in
  * one persistent kernel that reads a queue in host-mapped memory, and each
  * result stays in its slot until opmos_server_poll collects it. submit
  * computes the query's heuristic on the SMs the resident kernel leaves free;

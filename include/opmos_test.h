@@ -47,8 +47,10 @@ OPMOS_API int opmos_test_merge(uint32_t d, uint32_t nfront, const uint32_t* fron
  * then the decision of every entry. Entries hold F = (f0, f1) (one label per
  * entry, two objectives, heuristic 0); dead[i] != 0 marks a label pruned in an
  * earlier step (dropped by the lazy OPEN delete).
- *   bins: b0, b1, s1, delta (the histogram's F[0] origin, F[1] origin and
- *     shift of the split buckets, F[0] bucket width; delta >= 1, s1 < 32).
+ *   bins: b0, b1, s1, delta, s2: an entry's cell is q * 256 + x with
+ *     q = (f0 - b0) / delta (0 below b0) and x = min((f1 - b1) >> s1, 255)
+ *     (0 below b1); its bin is min(cell >> s2, 4095), bin 4095 never taken
+ *     (delta >= 1, s1 < 32, s2 <= 30).
  *   taken: n bytes, 1 for the entries of the window. *bstar: b*. */
 OPMOS_API int opmos_test_window(uint32_t n, const uint32_t* f0, const uint32_t* f1, const uint8_t* dead,
                                 uint32_t window, const uint32_t* bins, uint8_t* taken, uint32_t* bstar);

@@ -207,6 +207,7 @@ struct ArenaPlan {
   uint32_t label_cap, open_cap, win_cap, cand_cap, plog_cap, nslots;
   unsigned long long fpool_words;
   size_t bytes;
+  size_t fixed;  // the part that does not grow with the labels
 };
 
 int plan_arena(const opmos_graph* g, uint32_t D, uint32_t window, size_t budget, bool batch, ArenaPlan* pl) {
@@ -224,6 +225,7 @@ int plan_arena(const opmos_graph* g, uint32_t D, uint32_t window, size_t budget,
   size_t fixed = (n + 1) * (8 + 4 + 4 + 2 * (4 + 4 + 4 + 4 * (size_t)pl->nslots)) + 3 * kNB * 4 +
                  2 * (size_t)pl->cand_cap * (24 + 4 * D) + (size_t)pl->plog_cap * 4 * D +
                  2 * ((size_t)pl->plog_cap + ptiles) * 4 * D + kPSMax * 4 + 64 * 256;
+  pl->fixed = fixed;
   if (budget < fixed + (8u << 20))
     return fail(OPMOS_ERR_CAPACITY, "arena budget %zu too small (fixed part %zu)", budget, fixed);
   const size_t rem = budget - fixed;
@@ -1124,8 +1126,19 @@ int opmos_server_create(const opmos_graph* const* graphs, uint32_t ngraphs, cons
         return rc;
       }
     }
+    // a slot's search arena: 512 MiB, or what a query of label_budget labels
+    // needs (labels take 30% of the part that grows) when that is more
     ArenaPlan pl;
-    if (int rc = plan_arena(&sv->shape, sv->dmax, o.window, kServeSlotBytes, true, &pl)) {
+    size_t slot_budget = kServeSlotBytes;
+    if (o.label_budget) {
+      if (int rc = plan_arena(&sv->shape, sv->dmax, o.window, 1ull << 40, true, &pl)) {
+        delete sv;
+        return rc;
+      }
+      const size_t per_label = 4 * (size_t)sv->dmax + 20;
+      slot_budget = std::max<size_t>(slot_budget, pl.fixed + (8u << 20) + o.label_budget * per_label * 10 / 3);
+    }
+    if (int rc = plan_arena(&sv->shape, sv->dmax, o.window, slot_budget, true, &pl)) {
       delete sv;
       return rc;
     }

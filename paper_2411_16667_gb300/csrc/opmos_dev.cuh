@@ -10,7 +10,7 @@
 //              live entries (alpha(v) = G_OP(v) u G_CL(v), Sec. 3)
 //   OPEN       two unsorted arrays of 64-bit keys (F[0] << 32 | F[1]) with
 //              label ids beside them (the step's OPEN and the next one), and a
-//              histogram of each by lexicographic bucket of (F[0], F[1]) (the
+//              histogram of each by lexicographic cell of (F[0], F[1]) (the
 //              ordered batch extraction of Algorithm 2); with OPMOS_FLAG_FIFO
 //              the first array is a ring read oldest first instead
 //   candidates two sets (step parity): the candidates of one window, grouped by
@@ -32,16 +32,14 @@ namespace opmos {
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr uint32_t kAlive = 0xFFFFFFFFu;  // ldead of a label that has not been pruned
 constexpr int32_t kNil = -1;
-constexpr int kNB = 4096;    // histogram bins of one OPEN array
-constexpr int kRows = 8;     // lowest F[0] buckets of a histogram, each split by F[1]
-constexpr int kSub = 256;    // F[1] sub-bins of each of them
-constexpr int kSplit = kRows * kSub;  // bins [0, kSplit) are split, [kSplit, kNB-1) whole, kNB-1 overflow
+constexpr int kNB = 4096;    // histogram bins of one OPEN array (the last one collects the rest)
+constexpr int kSub = 256;    // F[1] cells per F[0] bucket; a bin is 2^s2 consecutive cells
 constexpr unsigned kChunk = 32;       // OPEN entries per extraction work item
 constexpr unsigned kRankQ = 1024;     // P entries per rank work item of an index rebuild
 constexpr unsigned kPSMax = 32768;    // largest P indexed by the sorted snapshot
 constexpr unsigned kHeavyFrontier = 512;  // frontiers this large are merged by a whole block
 constexpr unsigned kHeavyCands = 32;      // ... and so are nodes reached by more candidates in a step
-constexpr unsigned kNodeSlots = 32;      // candidate slots per node and step in batch mode
+constexpr unsigned kNodeSlots = 64;      // candidate slots per node and step in batch mode
 constexpr unsigned kNodeSlotsGrid = 128; // ... for a single query (whole-grid search)
 
 enum StatIdx {
@@ -98,12 +96,13 @@ struct CycleCtl {
   Hot<unsigned long long> min_key;  // smallest key among the entries carried over by extraction
   Hot<unsigned> win_count;          // labels of window i
   Hot<unsigned> win_min;            // smallest F[0] among them
+  Hot<unsigned> win_max;            // largest F[0] among them
   Hot<unsigned> cand_count;         // candidates of window i (merged in step i)
   Hot<unsigned> touched_count;      // nodes they reach with a small frontier (one warp each)
   Hot<unsigned> heavy_count;        // ... with a large frontier (one block each)
   Hot<unsigned> work_next;          // dynamic claims: index-rank items, light merges, extraction chunks
   Hot<unsigned> heavy_next;         // dynamic claims of heavy merges
-  Hot<unsigned> f1lo;               // F[1] range of the carried entries in the split buckets
+  Hot<unsigned> f1lo;               // F[1] range of the carried entries the histogram's bins cover
   Hot<unsigned> f1hi;
   Hot<unsigned> plen;               // P-log length every reader uses in step i
   Hot<unsigned> lbase;              // labels that existed when step i began
@@ -112,10 +111,10 @@ struct CycleCtl {
   unsigned tmax[3];                 // longest heavy merge, light merge, extraction item of step i (ns)
 };
 
-// Bins of one OPEN array's histogram: F[0] origin, F[1] origin and shift of
-// the split buckets, F[0] bucket width.
+// Bins of one OPEN array's histogram: F[0] origin, F[1] origin and shift,
+// F[0] bucket width, cells per bin (2^s2).
 struct BinLimits {
-  uint32_t b0, b1, s1, delta;
+  uint32_t b0, b1, s1, delta, s2;
 };
 
 // The P index as one step sees it (a pair indexed by step parity; step i

@@ -123,6 +123,8 @@ __device__ inline unsigned block_exclusive_scan(unsigned x, unsigned* s_warp, un
   return r;
 }
 
+constexpr unsigned kHC = 256;  // candidates a block merge holds at once
+
 struct Shared {
   unsigned hist[kNB];  // this block's share of the next OPEN's histogram
   unsigned warp[33];
@@ -130,32 +132,31 @@ struct Shared {
   unsigned pmax[3];
   unsigned claim;
   PIdx pd;             // the P index as this step sees it
-  // one batch of a heavy node's candidates, merged by the whole block
-  uint32_t mc[OPMOS_MAX_D][32];
-  uint32_t medge[32], mpar[32];
-  int mmine[32];
+  // the candidates of a block-merged node (up to kHC at a time)
+  uint32_t hc[OPMOS_MAX_D][kHC];
+  int hcid[kHC];
+  uint32_t hedge[kHC], hpar[kHC];
+  unsigned halive[kHC / 32], hkill[kHC / 32], hpkill[kHC / 32];
   int m_next;
-  unsigned mq_ncand, mq_next, m_more;
-  unsigned m_nb, m_alive, m_kill, m_pkill;
+  unsigned mq_ncand, mq_next, m_nb, m_ok, m_lb, m_cap;
+  unsigned long long m_fb;
   unsigned tmax[3];    // this block's longest heavy merge, light merge, extraction item (ns)
 };
 
-// Histogram bin of an OPEN key (F0 << 32 | F1): the F0 bucket q = (F0 - b0) /
-// delta; buckets q < kRows are split into kSub bins by F1 >> s1 (relative to
-// b1), buckets kRows.. are whole, the last bin collects the rest. Monotone in
-// lexicographic (F0, F1) order, so every prefix of bins is a lexicographic
-// prefix of OPEN.
+// Histogram bin of an OPEN key (F0 << 32 | F1): the key's cell is
+// q * kSub + x, q = (F0 - b0) / delta its F[0] bucket and x = (F1 - b1) >> s1
+// (at most kSub - 1) its F[1] cell; a bin is 2^s2 consecutive cells, and the
+// last bin collects every key beyond. Monotone in lexicographic (F0, F1)
+// order for F0 >= b0, so every prefix of bins is a lexicographic prefix of
+// OPEN.
 struct BinParams {
-  uint32_t b0, b1, s1, delta;
+  uint32_t b0, b1, s1, delta, s2;
 };
 __device__ __forceinline__ unsigned bin_of(uint64_t key, const BinParams& bp) {
   const uint32_t F0 = (uint32_t)(key >> 32), F1 = (uint32_t)key;
-  const uint32_t q = F0 > bp.b0 ? (F0 - bp.b0) / bp.delta : 0u;
-  if (q < (unsigned)kRows) {
-    const uint32_t x = F1 > bp.b1 ? (F1 - bp.b1) >> bp.s1 : 0u;
-    return q * kSub + min(x, (unsigned)kSub - 1);
-  }
-  return kSplit + min(q - kRows, (unsigned)(kNB - kSplit - 1));
+  const uint64_t q = F0 > bp.b0 ? (F0 - bp.b0) / bp.delta : 0u;
+  const uint32_t x = F1 > bp.b1 ? min((F1 - bp.b1) >> bp.s1, (unsigned)kSub - 1) : 0u;
+  return (unsigned)min((q * kSub + x) >> bp.s2, (uint64_t)(kNB - 1));
 }
 
 // Z-order ("Morton") comparison without interleaving: the dimension whose
@@ -242,6 +243,7 @@ struct Search {
     K.min_key.v = ~0ull;
     K.win_count.v = 0;
     K.win_min.v = kInf;
+    K.win_max.v = 0;
     K.cand_count.v = 0;
     K.touched_count.v = 0;
     K.heavy_count.v = 0;
@@ -295,7 +297,7 @@ struct Search {
     CycleCtl& K = C->cyc[0];
     K.lbase.v = 1;
     // the bins of OPEN_0's histogram put l_s in bin 0
-    C->bins[0] = BinLimits{h0, (uint32_t)key, 0u, P.delta};
+    C->bins[0] = BinLimits{h0, (uint32_t)key, 0u, P.delta, 0u};
     if (s != t && h0 != kInf) {  // start == goal: P = {l_s}; h(s) = inf: goal unreachable
       A.okey[0][0] = key;
       A.oid[0][0] = 0;
@@ -357,9 +359,12 @@ struct Search {
   }
 
   // Bins of the histogram of OPEN_{i+1}, from what step i-1 measured (the
-  // same on every block). Origin: the smallest F[0] among the entries carried
-  // into OPEN_i, window i (whose children merge i creates) and window i-1
-  // (whose children are OPEN_i's other entries).
+  // same on every block). F[0] origin: the smallest F[0] among the entries
+  // carried into OPEN_i, window i (whose children merge i creates) and window
+  // i-1 (whose children are OPEN_i's other entries). F[1] cells: the F[1]
+  // range of the entries carried into OPEN_i in 256 cells. Cells per bin: the
+  // bins cover the F[0] buckets from the origin to window i's largest F[0]
+  // and three times window i's F[0] extent beyond.
   __device__ BinParams next_bins(const CycleCtl& K) const {
     const unsigned long long mk = ld_volatile64(&K.min_key.v);
     const unsigned lo = ld_volatile(&K.f1lo.v), hi = ld_volatile(&K.f1hi.v);
@@ -371,6 +376,10 @@ struct Search {
     b.s1 = 0;
     while ((span >> b.s1) >= (unsigned)kSub) ++b.s1;
     b.delta = P.delta;
+    const uint32_t wmax = ld_volatile(&K.win_max.v), wmin = min(ld_volatile(&K.win_min.v), wmax);
+    const uint64_t rows = (wmax > b.b0 ? (wmax - b.b0) / b.delta : 0u) + 1 + 3ull * ((wmax - wmin) / b.delta + 1);
+    b.s2 = 0;
+    while (b.s2 < 30 && ((uint64_t)(kNB - 1) << b.s2) / kSub < rows) ++b.s2;
     return b;
   }
 
@@ -472,7 +481,7 @@ struct Search {
     const unsigned lane = lane_id();
     const unsigned L = P.lanes, G_per = 32 / L, grp = lane / L, gl = lane % L;
     unsigned long long kmin = ~0ull, pcmp = 0;
-    unsigned wmin = kInf, f1lo = kInf, f1hi = 0;
+    unsigned wmin = kInf, wmax = 0, f1lo = kInf, f1hi = 0;
     const unsigned nchunks = (n_in + kChunk - 1) / kChunk;
     for (unsigned r = 0; r < kChunk; r += 32) {
       const unsigned i = chunk + (r + lane) * nchunks;
@@ -520,6 +529,7 @@ struct Search {
           st[S_EXTRACTED]++;
           take = true;
           wmin = min(wmin, (uint32_t)(key >> 32));
+          wmax = max(wmax, (uint32_t)(key >> 32));
         } else {
           keep = true;  // window full: stays in OPEN for the next step
         }
@@ -533,7 +543,7 @@ struct Search {
           kmin = min(kmin, (unsigned long long)key);
           const unsigned b = bin_of(key, bpn);
           atomicAdd(&S.hist[b], 1u);
-          if (b < (unsigned)kSplit) {
+          if (b < (unsigned)kNB - 1) {
             f1lo = min(f1lo, (uint32_t)key);
             f1hi = max(f1hi, (uint32_t)key);
           }
@@ -552,11 +562,15 @@ struct Search {
     st[S_PCMP] += pcmp;
     kmin = warp_min64(kmin);
     wmin = warp_min(wmin);
+    wmax = warp_max(wmax);
     f1lo = warp_min(f1lo);
     f1hi = warp_max(f1hi);
     if (lane == 0) {
       if (kmin != ~0ull) atomicMin(&K1.min_key.v, kmin);
-      if (wmin != kInf) atomicMin(&K1.win_min.v, wmin);
+      if (wmin != kInf) {
+        atomicMin(&K1.win_min.v, wmin);
+        atomicMax(&K1.win_max.v, wmax);
+      }
       if (f1lo != kInf) {
         atomicMin(&K1.f1lo.v, f1lo);
         atomicMax(&K1.f1hi.v, f1hi);
@@ -870,7 +884,6 @@ struct Search {
                                unsigned long long pcmp, bool p_done = false) {
     const CandSet& cs = A.cs[cyc & 1u];
     const unsigned lane = lane_id();
-    const unsigned nxt = (cyc & 1u) ^ 1u;
     const bool is_goal = (v == G.n);
     if (!is_goal && !p_done && __any_sync(0xffffffffu, alive)) {
       uint32_t F[D];
@@ -939,25 +952,8 @@ struct Search {
           if (is_goal) {
 #pragma unroll
             for (int k = 0; k < D; ++k) A.plog[(size_t)k * A.plog_cap + plen + r] = c[k];
-          } else if (P.flags & OPMOS_FLAG_FIFO) {
-            // the ring's tail; positions [head, tail) of this step stay unread-over
-            const unsigned o = agg_inc(&C->fifo_tail.v);
-            if (o - fifo_head < A.open_cap) {
-              A.oid[0][o % A.open_cap] = id;
-              atomicMax(&K1.open_count.v, o + 1u);
-            } else {
-              set_error(C, OPMOS_ERR_CAPACITY);
-            }
           } else {
-            const uint64_t key = key_of(c, v);
-            const unsigned o = agg_inc(&K1.open_count.v);
-            if (o < A.open_cap) {
-              A.okey[nxt][o] = key;
-              A.oid[nxt][o] = id;
-              atomicAdd(&S.hist[bin_of(key, bpn)], 1u);
-            } else {
-              set_error(C, OPMOS_ERR_CAPACITY);
-            }
+            push_open(id, c, v, K1);
           }
         }
         if (is_goal && lane == 0) {
@@ -973,6 +969,32 @@ struct Search {
       st[S_INSERTED] += ns;
       st[S_FCMP] += fcmp;
       st[S_PCMP] += pcmp;
+    }
+  }
+
+  // A new label joins the next OPEN: the array of step i+1 (counted in its
+  // histogram) or, with OPMOS_FLAG_FIFO, the ring's tail (positions
+  // [head, tail) of this step are never written over).
+  __device__ __forceinline__ void push_open(uint32_t id, const uint32_t (&c)[D], uint32_t v, CycleCtl& K1) {
+    if (P.flags & OPMOS_FLAG_FIFO) {
+      const unsigned o = agg_inc(&C->fifo_tail.v);
+      if (o - fifo_head < A.open_cap) {
+        A.oid[0][o % A.open_cap] = id;
+        atomicMax(&K1.open_count.v, o + 1u);
+      } else {
+        set_error(C, OPMOS_ERR_CAPACITY);
+      }
+      return;
+    }
+    const uint64_t key = key_of(c, v);
+    const unsigned o = agg_inc(&K1.open_count.v);
+    if (o < A.open_cap) {
+      const unsigned nxt = (cyc & 1u) ^ 1u;
+      A.okey[nxt][o] = key;
+      A.oid[nxt][o] = id;
+      atomicAdd(&S.hist[bin_of(key, bpn)], 1u);
+    } else {
+      set_error(C, OPMOS_ERR_CAPACITY);
     }
   }
 
@@ -1036,62 +1058,93 @@ struct Search {
     } while (cursor_more(q));
   }
 
-  // Merge of a node with a large frontier by the whole block (every thread
-  // calls it). Batches of up to 32 candidates as in merge_batch; warp 0
-  // gathers a batch and resolves it in itself (a), then all warps scan the
-  // frontier (b) in rounds of nwarps * 32 * kUH entries, each warp kUH tiles
-  // of 32, and compact it in place: a round's reads all precede the first
-  // barrier, its writes land below the round's start, so they never overwrite
-  // an entry another warp still has to read. Candidates killed by one warp
-  // are dropped by the others from the next round on. A candidate that a
-  // frontier entry weakly dominates never dominates another entry (the
-  // frontier is an antichain), so the entries each candidate prunes do not
-  // depend on when its death is seen. Warp 0 then runs (c)-(d).
+  // Merge of a node with a large frontier, or many candidates, by the whole
+  // block (every thread calls it). Up to kHC candidates at a time sit in
+  // shared memory (the node's slots, then its list):
+  //  (a) every thread resolves one candidate against all the others (strict
+  //      dominance; of equal ones the smallest arc id stays);
+  //  (b) all warps scan the frontier in rounds of nwarps * 32 * kUH entries,
+  //      each warp kUH tiles of 32 against every live candidate, and compact
+  //      it in place: a round's reads all precede the first barrier, its
+  //      writes land below the round's start, so they never overwrite an
+  //      entry another warp still has to read. Candidates killed by one warp
+  //      are dropped by the others from the next round on; a candidate that a
+  //      frontier entry weakly dominates never dominates another entry (the
+  //      frontier is an antichain), so the entries each candidate prunes do
+  //      not depend on when its death is seen;
+  //  (c) F against P, 32 candidates per warp, the P log tail and the index
+  //      tiles split between the warps that hold the same candidates;
+  //  (d) survivors become labels, join alpha(v) and the next OPEN.
   __device__ void merge_heavy(uint32_t v, CycleCtl& K1) {
     constexpr int U = kUH;
+    constexpr unsigned NW = kHC / 32;  // candidate words
     const CandSet& cs = A.cs[cyc & 1u];
-    const unsigned lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5, nw = blockDim.x >> 5;
     if (w == 0) {
       const Cursor q = open_cursor(cs, v);
       if (lane == 0) {
         S.mq_ncand = q.ncand;
-        S.mq_next = q.next;
+        S.mq_next = 0;
         S.m_next = q.list;
-        S.m_more = 1;
       }
     }
+    __syncthreads();
+    const unsigned in_slots = min(S.mq_ncand, A.nslots);
     for (;;) {
-      __syncthreads();
-      if (!S.m_more) break;
-      __syncthreads();  // every thread has read m_more before warp 0 moves it
-      if (w == 0) {
-        Cursor q{S.mq_ncand, S.mq_next, S.m_next};
-        unsigned nb = 0;
-        const int mine = next_batch(cs, v, q, &nb);
-        const bool valid = lane < nb;
-        uint32_t c[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) c[k] = valid ? cs.cg[(size_t)k * A.cand_cap + mine] : 0u;
-        const uint32_t my_edge = valid ? cs.cedge[mine] : kInf;
-        const bool alive = in_batch_alive(c, my_edge, valid, nb);
-#pragma unroll
-        for (int k = 0; k < D; ++k) S.mc[k][lane] = c[k];
-        S.mmine[lane] = mine;
-        S.medge[lane] = my_edge;
-        S.mpar[lane] = valid ? cs.cparent[mine] : kInf;
-        const unsigned a0 = __ballot_sync(0xffffffffu, alive);
-        if (lane == 0) {
-          S.mq_next = q.next;
-          S.m_next = q.list;
-          S.m_more = cursor_more(q) ? 1u : 0u;
-          S.m_nb = nb;
-          S.m_alive = a0;
-          S.m_kill = 0;
-          S.m_pkill = 0;
+      // gather the next (up to kHC) candidates: slots in parallel, then the list
+      const unsigned s0 = S.mq_next;
+      const unsigned take = s0 < in_slots ? min(kHC, in_slots - s0) : 0u;
+      if (tid < take) S.hcid[tid] = cs.cslot[(size_t)v * A.nslots + s0 + tid];
+      __syncthreads();  // every thread has read mq_next
+      if (tid == 0) {
+        unsigned n = take;
+        int cc = S.m_next;
+        while (cc != kNil && n < kHC) {
+          S.hcid[n++] = cc;
+          cc = cs.cnext[cc];
         }
+        S.m_next = cc;
+        S.mq_next = s0 + take;
+        S.m_nb = n;
       }
       __syncthreads();
-      unsigned a = S.m_alive;
+      const unsigned nb = S.m_nb;
+      if (nb == 0) break;
+      const unsigned nwords = (nb + 31) / 32;
+      if (tid < nb) {
+        const int c = S.hcid[tid];
+#pragma unroll
+        for (int k = 0; k < D; ++k) S.hc[k][tid] = cs.cg[(size_t)k * A.cand_cap + c];
+        S.hedge[tid] = cs.cedge[c];
+        S.hpar[tid] = cs.cparent[c];
+      }
+      if (tid < NW) {
+        S.hkill[tid] = 0;
+        S.hpkill[tid] = 0;
+      }
+      __syncthreads();
+      // (a) in-set resolution, candidate tid
+      {
+        bool alive = tid < nb;
+        if (alive) {
+          uint32_t ct[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) ct[k] = S.hc[k][tid];
+          const uint32_t et = S.hedge[tid];
+          for (unsigned j = 0; j < nb && alive; ++j) {
+            if (j == tid) continue;
+            uint32_t cj[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) cj[k] = S.hc[k][j];
+            const uint32_t ej = S.hedge[j];
+            if (dominates<D>(cj, ct) || (equal<D>(cj, ct) && (ej < et || (ej == et && j < tid)))) alive = false;
+          }
+        }
+        const unsigned am = __ballot_sync(0xffffffffu, alive);
+        if (lane == 0 && w < NW) S.halive[w] = am;
+      }
+      __syncthreads();
+      // (b) the frontier
       const uint64_t fb = A.fbase[v];
       const unsigned cap = A.fcap[v];
       const unsigned fc = A.fcount[v];
@@ -1110,7 +1163,9 @@ struct Search {
           for (int k = 0; k < D; ++k) m[u][k] = vm ? A.fpool[fb + (size_t)k * cap + i] : kInf;
           mid[u] = vm ? A.fpool[fb + (size_t)D * cap + i] : 0u;
         }
-        unsigned kill = 0, km[U], wtot = 0;
+        unsigned kill[NW], km[U], wtot = 0;
+#pragma unroll
+        for (unsigned q = 0; q < NW; ++q) kill[q] = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const unsigned i0 = base + u * 32;
@@ -1118,22 +1173,29 @@ struct Search {
           const bool vm = i < fc;
           const bool fresh = vm && mid[u] >= lbase;
           bool pruned = false;
-          unsigned am = i0 < fc ? (a & ~kill) : 0u;
-          if (i0 < fc) fcmp += (unsigned long long)__popc(am) * min(32u, fc - i0);
-          while (am) {
-            const unsigned j = __ffs(am) - 1;
-            am &= am - 1;
-            uint32_t cj[D];
+          if (i0 < fc) {
 #pragma unroll
-            for (int k = 0; k < D; ++k) cj[k] = S.mc[k][j];
-            const bool le_mc = vm && weakly_le<D>(m[u], cj);
-            const bool le_cm = vm && weakly_le<D>(cj, m[u]);
-            if (__ballot_sync(0xffffffffu, le_mc)) kill |= 1u << j;
-            if (fresh && le_mc && le_cm && S.medge[j] < A.ledge[mid[u]]) {
-              A.ledge[mid[u]] = S.medge[j];
-              A.lparent[mid[u]] = S.mpar[j];
+            for (unsigned q = 0; q < NW; ++q) {
+              if (q >= nwords) break;
+              unsigned am = S.halive[q] & ~S.hkill[q] & ~kill[q];
+              fcmp += (unsigned long long)__popc(am) * min(32u, fc - i0);
+              while (am) {
+                const unsigned j = __ffs(am) - 1;
+                am &= am - 1;
+                const unsigned jj = q * 32 + j;
+                uint32_t cj[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) cj[k] = S.hc[k][jj];
+                const bool le_mc = vm && weakly_le<D>(m[u], cj);
+                const bool le_cm = vm && weakly_le<D>(cj, m[u]);
+                if (__ballot_sync(0xffffffffu, le_mc)) kill[q] |= 1u << j;
+                if (fresh && le_mc && le_cm && S.hedge[jj] < A.ledge[mid[u]]) {
+                  A.ledge[mid[u]] = S.hedge[jj];
+                  A.lparent[mid[u]] = S.hpar[jj];
+                }
+                pruned |= le_cm && !le_mc;
+              }
             }
-            pruned |= le_cm && !le_mc;
           }
           if (vm && pruned) {
             A.ldead[mid[u]] = cyc;
@@ -1145,7 +1207,9 @@ struct Search {
         }
         if (lane == 0) {
           S.warp[w] = wtot;
-          if (kill) atomicOr(&S.m_kill, kill);
+#pragma unroll
+          for (unsigned q = 0; q < NW; ++q)
+            if (kill[q]) atomicOr(&S.hkill[q], kill[q]);
         }
         __syncthreads();  // (1) all reads of this round are done
         const unsigned x = lane < nw ? S.warp[lane] : 0u;
@@ -1157,7 +1221,6 @@ struct Search {
         }
         const unsigned wpre = __shfl_sync(0xffffffffu, incl - x, w);
         const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
-        a &= ~S.m_kill;
         unsigned pos = out + wpre;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -1171,48 +1234,121 @@ struct Search {
           }
           pos += __popc(km[u]);
         }
-        __syncthreads();  // (2) S.warp and S.m_kill read by every warp
+        bool any = false;
+#pragma unroll
+        for (unsigned q = 0; q < NW; ++q) any |= (S.halive[q] & ~S.hkill[q]) != 0;
+        __syncthreads();  // (2) S.warp and S.hkill read by every warp
         const unsigned seen = min(r0 + R, fc);
         out += total;
-        if (a == 0 && out == seen) {
+        if (!any && out == seen) {
           // no candidate left to test and nothing moved: the rest stays in place
           out = fc;
           break;
         }
       }
       if (lane == 0) st[S_FCMP] += fcmp;
-      // (c) F against P, split over the block's warps: each scans its slice
-      // of the unindexed log tail and of the index tiles; a candidate any
-      // warp finds dominated is dropped
-      if (a) {
-        const PIdx& pd = S.pd;
-        uint32_t F[D];
+      // (c) F against P: warp w takes candidate word w % nwords and one of the
+      // nw / nwords slices of the P log tail and of the index tiles
+      {
+        const unsigned q = w % nwords, nsl = nw / nwords, sl = w / nwords;
+        const unsigned word = S.halive[q] & ~S.hkill[q];
+        if (word && sl < nsl) {
+          const PIdx& pd = S.pd;
+          const unsigned jj = q * 32 + lane;
+          uint32_t F[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) F[k] = S.mc[k][lane] + hk(k, v);
-        bool alive = (a >> lane) & 1u;
-        const unsigned t0 = pd.count ? pd.mark : 0u, t1 = psnap;
-        const unsigned tper = ((t1 - min(t0, t1) + nw - 1) / nw + 31) / 32 * 32;
-        const unsigned lo = min(t1, t0 + w * tper), hi = min(t1, lo + tper);
-        const unsigned nt = pd.count ? pd.ntiles : 0u;
-        const unsigned gper = ((nt + nw - 1) / nw + 31) / 32 * 32;
-        const unsigned glo = min(nt, w * gper), ghi = min(nt, glo + gper);
-        unsigned long long pcmp = 0;
-        p_filter(alive, F, lo, hi, pd.count, glo, ghi, nt, pd.cur, pcmp);
-        st[S_PCMP] += pcmp;
-        const unsigned pk = __ballot_sync(0xffffffffu, !alive) & a;
-        if (lane == 0 && pk) atomicOr(&S.m_pkill, pk);
+          for (int k = 0; k < D; ++k) F[k] = S.hc[k][jj] + hk(k, v);
+          bool alive = (word >> lane) & 1u;
+          const unsigned t0 = pd.count ? pd.mark : 0u, t1 = psnap;
+          const unsigned tper = ((t1 - min(t0, t1) + nsl - 1) / nsl + 31) / 32 * 32;
+          const unsigned lo = min(t1, t0 + sl * tper), hi = min(t1, lo + tper);
+          const unsigned nt = pd.count ? pd.ntiles : 0u;
+          const unsigned gper = ((nt + nsl - 1) / nsl + 31) / 32 * 32;
+          const unsigned glo = min(nt, sl * gper), ghi = min(nt, glo + gper);
+          unsigned long long pcmp = 0;
+          p_filter(alive, F, lo, hi, pd.count, glo, ghi, nt, pd.cur, pcmp);
+          st[S_PCMP] += pcmp;
+          const unsigned pk = __ballot_sync(0xffffffffu, !alive) & word;
+          if (lane == 0 && pk) atomicOr(&S.hpkill[q], pk);
+        }
       }
       __syncthreads();
-      a &= ~S.m_pkill;
-      if (w == 0) {
-        const unsigned nb = S.m_nb;
-        const bool valid = lane < nb;
-        uint32_t c[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) c[k] = S.mc[k][lane];
-        const bool alive = valid && ((a >> lane) & 1u);
-        merge_finish(v, S.mmine[lane], c, valid, alive, out, fb, cap, K1, 0ull, 0ull, true);
+      // (d) survivors become labels, join alpha(v) and the next OPEN
+      const bool surv = tid < nb && (((S.halive[w % NW] & ~S.hkill[w % NW] & ~S.hpkill[w % NW]) >> lane) & 1u);
+      const unsigned smask = __ballot_sync(0xffffffffu, surv);
+      if (lane == 0) S.warp[w] = __popc(smask);
+      __syncthreads();
+      unsigned pre = 0, ntot = 0;
+      for (unsigned q = 0; q < nw; ++q) {
+        const unsigned c = S.warp[q];
+        pre += q < w ? c : 0u;
+        ntot += c;
       }
+      const unsigned rank = pre + __popc(smask & lanemask_lt());
+      if (tid == 0) {
+        S.m_ok = 0;
+        S.m_fb = fb;
+        S.m_cap = cap;
+        if (ntot) {
+          const unsigned lb = atomicAdd(&C->n_labels.v, ntot);
+          S.m_lb = lb;
+          if (lb + ntot > A.label_cap || lb + ntot > P.label_budget) {
+            set_error(C, (lb + ntot > A.label_cap) ? OPMOS_ERR_CAPACITY : OPMOS_ERR_BUDGET);
+          } else {
+            atomicMax(&K1.lbase.v, lb + ntot);
+            S.m_ok = 1;
+            if (out + ntot > cap) {  // grow: a new block of twice the size
+              const unsigned tile = P.tile;
+              unsigned ncap = max(2u * (out + ntot), tile);
+              ncap = (ncap + tile - 1) / tile * tile;
+              const unsigned long long nb0 = atomicAdd(&C->f_words.v, (unsigned long long)(D + 1) * ncap);
+              if (nb0 + (unsigned long long)(D + 1) * ncap > A.fpool_words) {
+                set_error(C, OPMOS_ERR_CAPACITY);
+                S.m_ok = 0;
+              } else {
+                S.m_fb = nb0;
+                S.m_cap = ncap;
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (S.m_ok) {
+        const uint64_t nfb = S.m_fb;
+        const unsigned ncap = S.m_cap;
+        if (nfb != fb) {
+          for (unsigned x = tid; x < out; x += blockDim.x)
+#pragma unroll
+            for (int k = 0; k <= D; ++k) A.fpool[nfb + (size_t)k * ncap + x] = A.fpool[fb + (size_t)k * cap + x];
+        }
+        if (surv) {
+          const unsigned id = S.m_lb + rank;
+          uint32_t c[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) c[k] = S.hc[k][tid];
+#pragma unroll
+          for (int k = 0; k < D; ++k) A.lg[(size_t)k * A.label_cap + id] = c[k];
+          A.lnode[id] = v;
+          A.lparent[id] = S.hpar[tid];
+          A.ledge[id] = S.hedge[tid];
+          A.lpver[id] = psnap;
+          A.ldead[id] = kAlive;
+#pragma unroll
+          for (int k = 0; k < D; ++k) A.fpool[nfb + (size_t)k * ncap + out + rank] = c[k];
+          A.fpool[nfb + (size_t)D * ncap + out + rank] = id;
+          push_open(id, c, v, K1);
+        }
+        if (tid == 0) {
+          A.fbase[v] = nfb;
+          A.fcap[v] = ncap;
+          A.fcount[v] = out + ntot;
+          st[S_INSERTED] += ntot;
+        }
+      } else if (tid == 0) {
+        A.fcount[v] = out;
+      }
+      __syncthreads();  // the next group reuses the shared candidate arrays
     }
   }
 
@@ -1347,7 +1483,7 @@ struct Search {
     psnap = ld_volatile(&K0.plen.v);
     lbase = ld_volatile(&K0.lbase.v);
     const BinLimits bl = C->bins[r0];
-    const BinParams bp{bl.b0, bl.b1, bl.s1, bl.delta};  // bins OPEN_i's histogram was built on
+    const BinParams bp{bl.b0, bl.b1, bl.s1, bl.delta, bl.s2};  // bins OPEN_i's histogram was built on
     bpn = next_bins(K0);
     for (unsigned x = threadIdx.x; x < kNB; x += blockDim.x) S.hist[x] = 0;
     if (threadIdx.x == 0) {
@@ -1375,7 +1511,7 @@ struct Search {
         atomicMax(&K1.plen.v, psnap);
         atomicMax(&K1.lbase.v, lbase);
         K1.win_min_prev = ld_volatile(&K0.win_min.v);
-        C->bins[r1] = BinLimits{bpn.b0, bpn.b1, bpn.s1, bpn.delta};
+        C->bins[r1] = BinLimits{bpn.b0, bpn.b1, bpn.s1, bpn.delta, bpn.s2};
         if (fifo) {
           K1.head = head + fwin;
           atomicMax(&K1.open_count.v, head + n_in);

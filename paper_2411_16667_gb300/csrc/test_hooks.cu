@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kGridThreads, 1) merge_hook_kernel(GraphDev G,
   X.cyc = 0;
   X.psnap = 0;
   X.lbase = lbase;
-  X.bpn = BinParams{0u, 0u, 0u, 1u};
+  X.bpn = BinParams{0u, 0u, 0u, 1u, 0u};
   if (threadIdx.x == 0) {
     S.pd = PIdx{};
     for (int i = 0; i < kNB; ++i) S.hist[i] = 0;
@@ -282,7 +282,7 @@ int opmos_test_window(uint32_t n, const uint32_t* f0, const uint32_t* f1, const 
                       const uint32_t* bins, uint8_t* taken, uint32_t* bstar) {
   try {
     if (!taken || !bstar || !bins || (n && (!f0 || !f1 || !dead))) return hook_fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
-    if (bins[3] == 0 || bins[2] >= 32 || window == 0 || n > (1u << 22))
+    if (bins[3] == 0 || bins[2] >= 32 || bins[4] > 30 || window == 0 || n > (1u << 22))
       return hook_fail(OPMOS_ERR_INVALID_ARG, "bad window, bins or size");
     constexpr int D = 2;
     const uint32_t cap = n + 64;
@@ -381,7 +381,7 @@ int opmos_test_window(uint32_t n, const uint32_t* f0, const uint32_t* f1, const 
     P.label_budget = cap;
     P.qd = D;
     P.ps_grow = 6;
-    const BinParams bp{bins[0], bins[1], bins[2], bins[3]};
+    const BinParams bp{bins[0], bins[1], bins[2], bins[3], bins[4]};
     OutPool O{nullptr, 0, nullptr};
     window_hist_kernel<<<64, 256>>>(A, n, bp, A.hist + 1 * kNB);
     window_hook_kernel<<<1, kGridThreads>>>(G, A, C, P, O, n, bp, d_bstar);

@@ -68,10 +68,7 @@ def test_missing_library_fails_loudly(tmp_path):
         opmos._lib = saved
 
 
-def test_plain_c_client_links_and_behaves(tmp_path):
-    """A C program built against the header alone and linked to the library:
-    defaults are filled in, and without a device compute calls fail with
-    OPMOS_ERR_CUDA and a message (with one, it checks a two-path front)."""
+def _run_c_client(tmp_path):
     lib = pkg.build()
     exe = tmp_path / "client"
     subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
@@ -79,3 +76,20 @@ def test_plain_c_client_links_and_behaves(tmp_path):
                            f"-Wl,-rpath,{os.path.dirname(lib)}", "-o", str(exe)])
     p = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert p.returncode == 0, f"exit {p.returncode}: {p.stdout} {p.stderr}"
+    return p.stdout
+
+
+def test_plain_c_client_links_and_behaves(tmp_path):
+    """A C program built against the header alone and linked to the library:
+    defaults are filled in, and without a device compute calls fail with
+    OPMOS_ERR_CUDA and a message (with one, it checks a two-path front)."""
+    _run_c_client(tmp_path)
+
+
+@pytest.mark.gpu
+def test_plain_c_client_solves_on_the_device(tmp_path):
+    """The same C program on a GPU: its device branch solves the two-path
+    graph of Sec. 1 and checks the front {(4,5), (5,4)} and a path."""
+    if opmos.opmos_device_count() == 0:
+        pytest.fail("no CUDA device visible to the library")
+    assert "front (4,5) (5,4)" in _run_c_client(tmp_path)

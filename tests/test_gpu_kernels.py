@@ -11,7 +11,8 @@ references of the same operation.
 * The window of the ordered extraction (Algorithm 2): the live entries in
   the histogram bins [0, b*], b* the largest bin whose cumulative count stays
   within W (at least the first non-empty one) -- and, independently of the
-  bins, a lexicographic prefix of the live entries.
+  bins, a lexicographic prefix of the live entries (of their F[0] bucket and
+  F[1]; with bucket width 1, of F).
 """
 import numpy as np
 import pytest
@@ -89,33 +90,33 @@ def test_node_merge_matches_host_reference(op, d, nf, nc, slots, block):
     assert got == _reference(front, cand, arc)
 
 
-NB, ROWS, SUB = 4096, 8, 256
+NB, SUB = 4096, 256
 
 
-def _bin(f0, f1, b0, b1, s1, delta):
-    """The histogram bin a search step assigns to F = (f0, f1): F[0] buckets
-    of width delta from b0, the 8 lowest split into 256 bins of F[1] >> s1
-    from b1, 2047 whole buckets after them, one bin for the rest."""
+def _bin(f0, f1, b0, b1, s1, delta, s2):
+    """The histogram bin a search step assigns to F = (f0, f1): cell
+    q * 256 + x with q the F[0] bucket (width delta from b0) and x the F[1]
+    cell (F[1] >> s1 from b1, at most 255); 2^s2 cells per bin; the last bin
+    collects the rest."""
     q = (f0 - b0) // delta if f0 > b0 else 0
-    if q < ROWS:
-        x = (f1 - b1) >> s1 if f1 > b1 else 0
-        return q * SUB + min(x, SUB - 1)
-    return ROWS * SUB + min(q - ROWS, NB - ROWS * SUB - 1)
+    x = min((f1 - b1) >> s1, SUB - 1) if f1 > b1 else 0
+    return min((q * SUB + x) >> s2, NB - 1)
 
 
-@pytest.mark.parametrize("n,window,spread,s1,delta,seed", [
-    (1000, 64, 30, 0, 1, 1), (1000, 256, 30, 2, 1, 2), (5000, 1024, 200, 3, 2, 3), (300, 5000, 10, 0, 1, 4),
-    (4000, 100, 3, 0, 1, 5), (20000, 2048, 2000, 6, 4, 6), (33, 1, 5, 0, 1, 7)])
-def test_window_is_a_lexicographic_prefix(op, n, window, spread, s1, delta, seed):
+@pytest.mark.parametrize("n,window,spread,s1,delta,s2,seed", [
+    (1000, 64, 30, 0, 1, 0, 1), (1000, 256, 30, 2, 1, 1, 2), (5000, 1024, 200, 3, 2, 3, 3),
+    (300, 5000, 10, 0, 1, 0, 4), (4000, 100, 3, 0, 1, 0, 5), (20000, 2048, 2000, 6, 4, 5, 6),
+    (33, 1, 5, 0, 1, 0, 7), (8000, 700, 60, 4, 1, 8, 8)])
+def test_window_is_a_lexicographic_prefix(op, n, window, spread, s1, delta, s2, seed):
     rng = np.random.default_rng(seed)
     f0 = (500 + rng.integers(0, spread, size=n)).astype(np.uint32)
     f1 = (7000 + rng.integers(0, 40 * spread, size=n)).astype(np.uint32)
     dead = rng.random(n) < 0.2
     b0, b1 = int(f0.min()), int(f1.min())
-    taken, bstar = op.opmos_test_window(f0, f1, dead, window, [b0, b1, s1, delta])
+    taken, bstar = op.opmos_test_window(f0, f1, dead, window, [b0, b1, s1, delta, s2])
     live = ~dead
     assert not np.any(taken & dead)
-    bins = np.array([_bin(int(a), int(b), b0, b1, s1, delta) for a, b in zip(f0, f1)])
+    bins = np.array([_bin(int(a), int(b), b0, b1, s1, delta, s2) for a, b in zip(f0, f1)])
     hist = np.bincount(bins[live], minlength=NB)
     cum = np.cumsum(hist)
     first = int(np.flatnonzero(hist[:NB - 1])[0])
@@ -123,8 +124,10 @@ def test_window_is_a_lexicographic_prefix(op, n, window, spread, s1, delta, seed
     exp_bstar = max(int(fit[-1]) if fit.size else 0, first)
     assert bstar == exp_bstar
     assert np.array_equal(taken, live & (bins <= exp_bstar))
-    # a lexicographic prefix of the live entries, whatever the bins
-    keys = (f0.astype(np.uint64) << np.uint64(32)) | f1.astype(np.uint64)
+    # a lexicographic prefix of the live entries in (F0 bucket, F1) order --
+    # (F0, F1) order when delta = 1 -- whatever the bins
+    q = (f0.astype(np.uint64) - np.uint64(b0)) // np.uint64(delta)
+    keys = (q << np.uint64(32)) | f1.astype(np.uint64)
     if taken.any() and (live & ~taken).any():
         assert keys[taken].max() < keys[live & ~taken].min()
     assert taken.sum() <= window or np.all(bins[taken] == first)

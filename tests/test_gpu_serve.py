@@ -93,3 +93,51 @@ def test_server_queue_full_is_reported(op):
     st, r = _wait(op, srv, [t])[t]
     assert st == op.OK and np.array_equal(r.costs, oracle.solve(g.first_objectives(1), 5, 900).costs)
     srv.close()
+
+
+def test_server_on_the_benchmark_graphs(op):
+    """Serving on the config-1, config-2 and config-3 graphs held resident
+    together: a stream of queries with objective counts up to each graph's d,
+    submitted at random intervals while earlier ones run. Every result must
+    equal the oracle's front: the 256x256 corner query at its full d = 3
+    against the committed oracle fixture, config-3 queries at d = 2 that the
+    oracle finishes within 300k labels, config-1 queries at d = 1 and 2."""
+    import os
+    from pins import check_front_sampled, load_front_fixture
+    meta, fx = load_front_fixture(os.path.join(os.path.dirname(__file__), "golden", "config2_seed1_q0.front"))
+    g1, _ = synth.config1()
+    g2, q2 = synth.config2()
+    g3, q3 = synth.config3()
+    assert g2.digest() == meta["digest"]
+    graphs = [g1, g2, g3]
+    rng = np.random.default_rng(11)
+    plan, expect = [], []
+    for _ in range(12):
+        d = int(rng.integers(1, 3))
+        s, t = (int(x) for x in rng.integers(0, g1.n, size=2))
+        plan.append((0, d, s, t))
+        expect.append(oracle.solve(g1.first_objectives(d), s, t).costs)
+    for i in range(16):
+        s, t = q3[i]
+        f = oracle.solve(g3.first_objectives(2), s, t, label_budget=300_000, partial_ok=True)
+        if not f.stats["partial"]:
+            plan.append((2, 2, s, t))
+            expect.append(f.costs)
+    for _ in range(2):
+        plan.append((1, 3, q2[0][0], q2[0][1]))
+        expect.append(fx)
+    order = rng.permutation(len(plan))
+    G = [op.opmos_graph.from_synth(g) for g in graphs]
+    srv = op.opmos_server(G, label_budget=25_000_000, window=1024)
+    tickets = {}
+    for k in order:
+        tickets[int(k)] = srv.submit(*plan[k])
+        time.sleep(float(rng.exponential(0.01)))
+    done = _wait(op, srv, list(tickets.values()), timeout=300.0)
+    srv.close()
+    assert sum(1 for p in plan if p[0] == 2) >= 4
+    for k, (gi, d, s, t) in enumerate(plan):
+        st, r = done[tickets[k]]
+        assert st == op.OK, f"query {(gi, d, s, t)} status {st}"
+        assert np.array_equal(r.costs, expect[k]), f"query {(gi, d, s, t)}: front differs from the oracle"
+        check_front_sampled(graphs[gi].first_objectives(d), s, t, r.costs, r.paths, nrows=300, npaths=60)
