@@ -23,9 +23,10 @@ extern "C" {
  * frontier checks -- a candidate weakly dominated by a frontier label is
  * dropped, frontier labels a candidate strictly dominates are pruned -- and
  * the in-batch resolution of Sec. 5's Dup&Dom), exactly as a search step runs
- * it on the device: one warp (block = 0) or one whole thread block
- * (block = 1), candidates taken 32 at a time from the node's slots and then
- * its overflow list. The frontier must be mutually non-dominated and
+ * it on the device: one warp (block = 0), one whole thread block
+ * (block = 1), or a block merge split over `block` = 2..4 ranges of the
+ * frontier (run one after the other; the last one finishes the node), with
+ * candidates taken from the node's slots and then its overflow list. The frontier must be mutually non-dominated and
  * cost-unique, as in a search. No solution set is involved.
  *   d: 1, 2, 3, 4, 5, 8, 12 or 16 (other values: OPMOS_ERR_INVALID_ARG).
  *   front: nfront*d costs, row-major (labels that existed before the step).

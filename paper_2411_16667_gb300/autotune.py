@@ -23,7 +23,9 @@ import numpy as np
 
 from . import opmos
 
-WINDOWS_SINGLE = (256, 512, 1024, 2048)
+# single queries: up to windows that take all of OPEN each step (on a
+# latency-bound search, fewer and larger steps can win despite extra labels)
+WINDOWS_SINGLE = (256, 1024, 4096, 16384, 65536, 262144)
 WINDOWS_BATCH = (64, 256, 1024)
 LANES = (4, 8, 16)
 TILES = (32, 64)

@@ -220,10 +220,11 @@ int plan_arena(const opmos_graph* g, uint32_t D, uint32_t window, size_t budget,
   pl->plog_cap = batch ? (1u << 16) : (1u << 20);
   const size_t ptiles = pl->plog_cap / 32 + 1;
   // per node: fbase, fcount, fcap, then per candidate set ncand, node_head, slots;
-  // per candidate (two sets): node, parent, arc, list link, two touched entries, cost vector
+  // per candidate (two sets): node, parent, arc, list link, two touched entries, split count,
+  // flag, cost vector
   pl->nslots = batch ? kNodeSlots : kNodeSlotsGrid;
-  size_t fixed = (n + 1) * (8 + 4 + 4 + 2 * (4 + 4 + 4 + 4 * (size_t)pl->nslots)) + 3 * kNB * 4 +
-                 2 * (size_t)pl->cand_cap * (24 + 4 * D) + (size_t)pl->plog_cap * 4 * D +
+  size_t fixed = (n + 1) * (8 + 4 + 4 + 2 * (4 + 4 + 4 + 4 + 4 * (size_t)pl->nslots)) + 3 * kNB * 4 +
+                 2 * (size_t)pl->cand_cap * (32 + 4 * D) + (size_t)pl->plog_cap * 4 * D +
                  2 * ((size_t)pl->plog_cap + ptiles) * 4 * D + kPSMax * 4 + 64 * 256;
   pl->fixed = fixed;
   if (budget < fixed + (8u << 20))
@@ -251,6 +252,9 @@ void layout_arena(const opmos_graph* g, uint32_t D, const ArenaPlan& pl, char* b
     cs.ncand = carve<uint32_t>(p, n);
     cs.node_head = carve<int32_t>(p, n);
     cs.hflag = carve<uint32_t>(p, n);
+    cs.hcnt = carve<uint32_t>(p, n);
+    cs.hsplit = carve<uint32_t>(p, pl.cand_cap);
+    cs.cflag = carve<uint32_t>(p, pl.cand_cap);
     cs.cslot = carve<int32_t>(p, n * pl.nslots);
     cs.cnode = carve<uint32_t>(p, pl.cand_cap);
     cs.cparent = carve<uint32_t>(p, pl.cand_cap);

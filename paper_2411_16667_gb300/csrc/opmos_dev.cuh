@@ -39,6 +39,8 @@ constexpr unsigned kRankQ = 1024;     // P entries per rank work item of an inde
 constexpr unsigned kPSMax = 32768;    // largest P indexed by the sorted snapshot
 constexpr unsigned kHeavyFrontier = 512;  // frontiers this large are merged by a whole block
 constexpr unsigned kHeavyCands = 32;      // ... and so are nodes reached by more candidates in a step
+constexpr unsigned kSplitMin = 1024;      // frontier entries per block when a block merge is split
+constexpr unsigned kSplitMax = 4;         // ... over at most this many blocks
 constexpr unsigned kNodeSlots = 64;      // candidate slots per node and step in batch mode
 constexpr unsigned kNodeSlotsGrid = 128; // ... for a single query (whole-grid search)
 
@@ -156,6 +158,9 @@ struct CandSet {
   int32_t* cslot;      // (n+1) * nslots: the first nslots of them
   int32_t* node_head;  // n+1: the rest, linked by cnext
   uint32_t* hflag;     // n+1: the node is merged by a whole block (listed once among the heavy nodes)
+  uint32_t* hcnt;      // n+1: ranges of a split block merge finished so far
+  uint32_t* hsplit;    // cand_cap: blocks the h-th heavy node's merge is split over
+  uint32_t* cflag;     // cand_cap: candidate dropped by a split merge's range pass
   uint32_t* cnode;
   uint32_t* cparent;
   uint32_t* cedge;

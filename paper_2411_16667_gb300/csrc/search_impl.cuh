@@ -232,6 +232,7 @@ struct Search {
         A.cs[b].node_head[v] = kNil;
         A.cs[b].ncand[v] = 0;
         A.cs[b].hflag[v] = 0;
+        A.cs[b].hcnt[v] = 0;
       }
     }
     for (unsigned i = T.tid(); i < 3u * kNB; i += T.nthreads()) A.hist[i] = 0;
@@ -396,6 +397,7 @@ struct Search {
     cs.cnode[c] = v2;
     cs.cparent[c] = parent;
     cs.cedge[c] = e;
+    cs.cflag[c] = 0u;
 #pragma unroll
     for (int k = 0; k < D; ++k) cs.cg[(size_t)k * A.cand_cap + c] = g2[k];
     const unsigned pos = atomicAdd(&cs.ncand[v2], 1u);
@@ -416,8 +418,12 @@ struct Search {
     const bool heavy = v2 != G.n && ((pos == 0 && A.fcount[v2] >= kHeavyFrontier) ||
                                      (pos == kHeavyCands / 2 - 1 && A.fcount[v2] >= kHeavyFrontier * 3 / 8) ||
                                      pos == kHeavyCands);
-    if (heavy && atomicExch(&cs.hflag[v2], 1u) == 0u)
-      cs.touched[2u * A.cand_cap - 1u - atomicAdd(&K1.heavy_count.v, 1u)] = v2;
+    if (heavy && atomicExch(&cs.hflag[v2], 1u) == 0u) {
+      const unsigned h = atomicAdd(&K1.heavy_count.v, 1u);
+      cs.touched[2u * A.cand_cap - 1u - h] = v2;
+      // a frontier this large is scanned by several blocks (merge_range)
+      cs.hsplit[h] = min(kSplitMax, max(1u, A.fcount[v2] / kSplitMin));
+    }
   }
 
   // Expansion of up to 32 / L window labels, one per lane group of L lanes
@@ -1076,19 +1082,26 @@ struct Search {
   //      tiles split between the warps that hold the same candidates;
   //  (d) survivors become labels, join alpha(v) and the next OPEN.
   __device__ void merge_heavy(uint32_t v, CycleCtl& K1) {
-    constexpr int U = kUH;
-    constexpr unsigned NW = kHC / 32;  // candidate words
     const CandSet& cs = A.cs[cyc & 1u];
-    const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5, nw = blockDim.x >> 5;
-    if (w == 0) {
+    if (threadIdx.x < 32) {
       const Cursor q = open_cursor(cs, v);
-      if (lane == 0) {
+      if (threadIdx.x == 0) {
         S.mq_ncand = q.ncand;
         S.mq_next = 0;
         S.m_next = q.list;
       }
     }
     __syncthreads();
+    heavy_groups(v, K1);
+  }
+
+  // The group loop of a block merge, from the cursor in shared memory
+  // (S.mq_ncand candidates, slots from S.mq_next, then the list at S.m_next).
+  __device__ void heavy_groups(uint32_t v, CycleCtl& K1) {
+    constexpr int U = kUH;
+    constexpr unsigned NW = kHC / 32;  // candidate words
+    const CandSet& cs = A.cs[cyc & 1u];
+    const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5, nw = blockDim.x >> 5;
     const unsigned in_slots = min(S.mq_ncand, A.nslots);
     for (;;) {
       // gather the next (up to kHC) candidates: slots in parallel, then the list
@@ -1275,81 +1288,306 @@ struct Search {
       __syncthreads();
       // (d) survivors become labels, join alpha(v) and the next OPEN
       const bool surv = tid < nb && (((S.halive[w % NW] & ~S.hkill[w % NW] & ~S.hpkill[w % NW]) >> lane) & 1u);
-      const unsigned smask = __ballot_sync(0xffffffffu, surv);
-      if (lane == 0) S.warp[w] = __popc(smask);
-      __syncthreads();
-      unsigned pre = 0, ntot = 0;
-      for (unsigned q = 0; q < nw; ++q) {
-        const unsigned c = S.warp[q];
-        pre += q < w ? c : 0u;
-        ntot += c;
-      }
-      const unsigned rank = pre + __popc(smask & lanemask_lt());
-      if (tid == 0) {
-        S.m_ok = 0;
-        S.m_fb = fb;
-        S.m_cap = cap;
-        if (ntot) {
-          const unsigned lb = atomicAdd(&C->n_labels.v, ntot);
-          S.m_lb = lb;
-          if (lb + ntot > A.label_cap || lb + ntot > P.label_budget) {
-            set_error(C, (lb + ntot > A.label_cap) ? OPMOS_ERR_CAPACITY : OPMOS_ERR_BUDGET);
-          } else {
-            atomicMax(&K1.lbase.v, lb + ntot);
-            S.m_ok = 1;
-            if (out + ntot > cap) {  // grow: a new block of twice the size
-              const unsigned tile = P.tile;
-              unsigned ncap = max(2u * (out + ntot), tile);
-              ncap = (ncap + tile - 1) / tile * tile;
-              const unsigned long long nb0 = atomicAdd(&C->f_words.v, (unsigned long long)(D + 1) * ncap);
-              if (nb0 + (unsigned long long)(D + 1) * ncap > A.fpool_words) {
-                set_error(C, OPMOS_ERR_CAPACITY);
-                S.m_ok = 0;
-              } else {
-                S.m_fb = nb0;
-                S.m_cap = ncap;
-              }
+      heavy_insert(v, K1, surv, out, fb, cap);
+      __syncthreads();  // the next group reuses the shared candidate arrays
+    }
+  }
+
+  // Survivors of a block merge (thread tid holds candidate tid in shared
+  // memory; surv tells whether it survived) become labels, join alpha(v) --
+  // out live entries at fb, cap, grown when full -- and the next OPEN.
+  __device__ void heavy_insert(uint32_t v, CycleCtl& K1, bool surv, unsigned out, uint64_t fb, unsigned cap) {
+    const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5, nw = blockDim.x >> 5;
+    const unsigned smask = __ballot_sync(0xffffffffu, surv);
+    if (lane == 0) S.warp[w] = __popc(smask);
+    __syncthreads();
+    unsigned pre = 0, ntot = 0;
+    for (unsigned q = 0; q < nw; ++q) {
+      const unsigned c = S.warp[q];
+      pre += q < w ? c : 0u;
+      ntot += c;
+    }
+    const unsigned rank = pre + __popc(smask & lanemask_lt());
+    if (tid == 0) {
+      S.m_ok = 0;
+      S.m_fb = fb;
+      S.m_cap = cap;
+      if (ntot) {
+        const unsigned lb = atomicAdd(&C->n_labels.v, ntot);
+        S.m_lb = lb;
+        if (lb + ntot > A.label_cap || lb + ntot > P.label_budget) {
+          set_error(C, (lb + ntot > A.label_cap) ? OPMOS_ERR_CAPACITY : OPMOS_ERR_BUDGET);
+        } else {
+          atomicMax(&K1.lbase.v, lb + ntot);
+          S.m_ok = 1;
+          if (out + ntot > cap) {  // grow: a new block of twice the size
+            const unsigned tile = P.tile;
+            unsigned ncap = max(2u * (out + ntot), tile);
+            ncap = (ncap + tile - 1) / tile * tile;
+            const unsigned long long nb0 = atomicAdd(&C->f_words.v, (unsigned long long)(D + 1) * ncap);
+            if (nb0 + (unsigned long long)(D + 1) * ncap > A.fpool_words) {
+              set_error(C, OPMOS_ERR_CAPACITY);
+              S.m_ok = 0;
+            } else {
+              S.m_fb = nb0;
+              S.m_cap = ncap;
             }
           }
         }
       }
-      __syncthreads();
-      if (S.m_ok) {
-        const uint64_t nfb = S.m_fb;
-        const unsigned ncap = S.m_cap;
-        if (nfb != fb) {
-          for (unsigned x = tid; x < out; x += blockDim.x)
-#pragma unroll
-            for (int k = 0; k <= D; ++k) A.fpool[nfb + (size_t)k * ncap + x] = A.fpool[fb + (size_t)k * cap + x];
-        }
-        if (surv) {
-          const unsigned id = S.m_lb + rank;
-          uint32_t c[D];
-#pragma unroll
-          for (int k = 0; k < D; ++k) c[k] = S.hc[k][tid];
-#pragma unroll
-          for (int k = 0; k < D; ++k) A.lg[(size_t)k * A.label_cap + id] = c[k];
-          A.lnode[id] = v;
-          A.lparent[id] = S.hpar[tid];
-          A.ledge[id] = S.hedge[tid];
-          A.lpver[id] = psnap;
-          A.ldead[id] = kAlive;
-#pragma unroll
-          for (int k = 0; k < D; ++k) A.fpool[nfb + (size_t)k * ncap + out + rank] = c[k];
-          A.fpool[nfb + (size_t)D * ncap + out + rank] = id;
-          push_open(id, c, v, K1);
-        }
-        if (tid == 0) {
-          A.fbase[v] = nfb;
-          A.fcap[v] = ncap;
-          A.fcount[v] = out + ntot;
-          st[S_INSERTED] += ntot;
-        }
-      } else if (tid == 0) {
-        A.fcount[v] = out;
-      }
-      __syncthreads();  // the next group reuses the shared candidate arrays
     }
+    __syncthreads();
+    if (S.m_ok) {
+      const uint64_t nfb = S.m_fb;
+      const unsigned ncap = S.m_cap;
+      if (nfb != fb) {
+        for (unsigned x = tid; x < out; x += blockDim.x)
+#pragma unroll
+          for (int k = 0; k <= D; ++k) A.fpool[nfb + (size_t)k * ncap + x] = A.fpool[fb + (size_t)k * cap + x];
+      }
+      if (surv) {
+        const unsigned id = S.m_lb + rank;
+        uint32_t c[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) c[k] = S.hc[k][tid];
+#pragma unroll
+        for (int k = 0; k < D; ++k) A.lg[(size_t)k * A.label_cap + id] = c[k];
+        A.lnode[id] = v;
+        A.lparent[id] = S.hpar[tid];
+        A.ledge[id] = S.hedge[tid];
+        A.lpver[id] = psnap;
+        A.ldead[id] = kAlive;
+#pragma unroll
+        for (int k = 0; k < D; ++k) A.fpool[nfb + (size_t)k * ncap + out + rank] = c[k];
+        A.fpool[nfb + (size_t)D * ncap + out + rank] = id;
+        push_open(id, c, v, K1);
+      }
+      if (tid == 0) {
+        A.fbase[v] = nfb;
+        A.fcap[v] = ncap;
+        A.fcount[v] = out + ntot;
+        st[S_INSERTED] += ntot;
+      }
+    } else if (tid == 0) {
+      A.fcount[v] = out;
+    }
+  }
+
+  // Compaction of a frontier after a split merge: the entries whose label
+  // was pruned in this step (ldead == cyc, written by other blocks: read past
+  // L1) are removed; returns the live count. Rounds as in heavy_groups (b).
+  __device__ unsigned compact_pruned(uint64_t fb, unsigned cap, unsigned F) {
+    constexpr int U = kUH;
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned R = nw * 32u * U;
+    unsigned out = 0;
+    for (unsigned r0 = 0; r0 < F; r0 += R) {
+      const unsigned base = r0 + w * 32u * U;
+      uint32_t m[U][D];
+      uint32_t mid[U];
+      unsigned km[U], wtot = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const unsigned i = base + u * 32 + lane;
+        const bool vm = i < F;
+#pragma unroll
+        for (int k = 0; k < D; ++k) m[u][k] = vm ? A.fpool[fb + (size_t)k * cap + i] : 0u;
+        mid[u] = vm ? A.fpool[fb + (size_t)D * cap + i] : 0u;
+        km[u] = __ballot_sync(0xffffffffu, vm && __ldcg(A.ldead + mid[u]) != cyc);
+        wtot += __popc(km[u]);
+      }
+      if (lane == 0) S.warp[w] = wtot;
+      __syncthreads();  // (1) all reads of this round are done
+      const unsigned x = lane < nw ? S.warp[lane] : 0u;
+      unsigned incl = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += y;
+      }
+      const unsigned wpre = __shfl_sync(0xffffffffu, incl - x, w);
+      const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+      unsigned pos = out + wpre;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const unsigned i = base + u * 32 + lane;
+        const bool keep = (km[u] >> lane) & 1u;
+        const unsigned p = pos + __popc(km[u] & lanemask_lt());
+        if (keep && p != i) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) A.fpool[fb + (size_t)k * cap + p] = m[u][k];
+          A.fpool[fb + (size_t)D * cap + p] = mid[u];
+        }
+        pos += __popc(km[u]);
+      }
+      __syncthreads();  // (2) S.warp read by every warp
+      out += total;
+    }
+    return out;
+  }
+
+  // A block merge split over k blocks (a node whose frontier was large when
+  // it was listed): block r scans the frontier entries [r F / k, (r+1) F / k)
+  // against the node's slot candidates, read only -- it marks the entries a
+  // candidate strictly dominates as pruned (ldead = cyc) and flags the
+  // candidates a frontier entry weakly dominates -- and tests F against P
+  // for every k-th word of candidates; block 0 also flags the candidates the
+  // in-set resolution drops. The last of the k blocks to finish (a counter
+  // per node; nobody waits) compacts the frontier, inserts the unflagged
+  // candidates and then merges the node's list candidates, if any, as
+  // heavy_groups does. The candidates a block sees die in the same order as
+  // in one block's scan (an entry that weakly dominates a candidate is never
+  // strictly dominated by it, the frontier being an antichain), so the
+  // result is the same set.
+  __device__ void merge_range(uint32_t v, unsigned r, unsigned k, CycleCtl& K1) {
+    constexpr int U = kUH;
+    constexpr unsigned NW = kHC / 32;
+    const CandSet& cs = A.cs[cyc & 1u];
+    const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5, nw = blockDim.x >> 5;
+    const unsigned F = A.fcount[v];
+    const unsigned nb = min(cs.ncand[v], A.nslots);
+    const uint64_t fb = A.fbase[v];
+    const unsigned cap = A.fcap[v];
+    if (tid < nb) {
+      const int c = cs.cslot[(size_t)v * A.nslots + tid];
+      S.hcid[tid] = c;
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) S.hc[kk][tid] = cs.cg[(size_t)kk * A.cand_cap + c];
+      S.hedge[tid] = cs.cedge[c];
+      S.hpar[tid] = cs.cparent[c];
+    }
+    if (tid < NW) {
+      S.hkill[tid] = 0;
+      S.hpkill[tid] = 0;
+    }
+    __syncthreads();
+    const unsigned nwords = (nb + 31) / 32;
+    {  // (a) in-set resolution, candidate tid (every block alike)
+      bool alive = tid < nb;
+      if (alive) {
+        uint32_t ct[D];
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) ct[kk] = S.hc[kk][tid];
+        const uint32_t et = S.hedge[tid];
+        for (unsigned j = 0; j < nb && alive; ++j) {
+          if (j == tid) continue;
+          uint32_t cj[D];
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) cj[kk] = S.hc[kk][j];
+          const uint32_t ej = S.hedge[j];
+          if (dominates<D>(cj, ct) || (equal<D>(cj, ct) && (ej < et || (ej == et && j < tid)))) alive = false;
+        }
+      }
+      const unsigned am = __ballot_sync(0xffffffffu, alive);
+      if (lane == 0 && w < NW) S.halive[w] = am;
+    }
+    __syncthreads();
+    // (b) this block's range of the frontier, read only
+    const unsigned lo = (unsigned)((uint64_t)F * r / k), hi = (unsigned)((uint64_t)F * (r + 1) / k);
+    unsigned long long fcmp = 0;
+    for (unsigned r0 = lo + w * 32u * U; r0 < hi; r0 += nw * 32u * U) {
+      uint32_t m[U][D];
+      uint32_t mid[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const unsigned i = r0 + u * 32 + lane;
+        const bool vm = i < hi;
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) m[u][kk] = vm ? A.fpool[fb + (size_t)kk * cap + i] : kInf;
+        mid[u] = vm ? A.fpool[fb + (size_t)D * cap + i] : 0u;
+      }
+      unsigned kill[NW];
+#pragma unroll
+      for (unsigned q = 0; q < NW; ++q) kill[q] = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const unsigned i0 = r0 + u * 32;
+        const bool vm = i0 + lane < hi;
+        bool pruned = false;
+        if (i0 < hi) {
+#pragma unroll
+          for (unsigned q = 0; q < NW; ++q) {
+            if (q >= nwords) break;
+            unsigned am = S.halive[q] & ~S.hkill[q] & ~kill[q];
+            fcmp += (unsigned long long)__popc(am) * min(32u, hi - i0);
+            while (am) {
+              const unsigned j = __ffs(am) - 1;
+              am &= am - 1;
+              uint32_t cj[D];
+#pragma unroll
+              for (int kk = 0; kk < D; ++kk) cj[kk] = S.hc[kk][q * 32 + j];
+              const bool le_mc = vm && weakly_le<D>(m[u], cj);
+              const bool le_cm = vm && weakly_le<D>(cj, m[u]);
+              if (__ballot_sync(0xffffffffu, le_mc)) kill[q] |= 1u << j;
+              pruned |= le_cm && !le_mc;
+            }
+          }
+        }
+        if (vm && pruned) {
+          A.ldead[mid[u]] = cyc;
+          st[S_PRUNED]++;
+        }
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (unsigned q = 0; q < NW; ++q)
+          if (kill[q]) atomicOr(&S.hkill[q], kill[q]);
+      }
+    }
+    if (lane == 0) st[S_FCMP] += fcmp;
+    __syncthreads();
+    // (c) F against P for the candidate words q = r, r + k, ...: the block's
+    // warps split each word's P log tail and index tiles
+    const unsigned nq = r < nwords ? (nwords - r + k - 1) / k : 0u;
+    if (nq) {
+      const unsigned q = r + (w % nq) * k, nsl = nw / nq, sl = w / nq;
+      const unsigned word = S.halive[q] & ~S.hkill[q];
+      if (word && sl < nsl) {
+        const PIdx& pd = S.pd;
+        const unsigned jj = q * 32 + lane;
+        uint32_t F2[D];
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) F2[kk] = S.hc[kk][jj] + hk(kk, v);
+        bool alive = (word >> lane) & 1u;
+        const unsigned t0 = pd.count ? pd.mark : 0u, t1 = psnap;
+        const unsigned tper = ((t1 - min(t0, t1) + nsl - 1) / nsl + 31) / 32 * 32;
+        const unsigned plo = min(t1, t0 + sl * tper), phi = min(t1, plo + tper);
+        const unsigned nt = pd.count ? pd.ntiles : 0u;
+        const unsigned gper = ((nt + nsl - 1) / nsl + 31) / 32 * 32;
+        const unsigned glo = min(nt, sl * gper), ghi = min(nt, glo + gper);
+        unsigned long long pcmp = 0;
+        p_filter(alive, F2, plo, phi, pd.count, glo, ghi, nt, pd.cur, pcmp);
+        st[S_PCMP] += pcmp;
+        const unsigned pk = __ballot_sync(0xffffffffu, !alive) & word;
+        if (lane == 0 && pk) atomicOr(&S.hpkill[q], pk);
+      }
+    }
+    __syncthreads();
+    if (tid < nb) {
+      const unsigned q = tid >> 5, bit = 1u << (tid & 31);
+      if (((S.hkill[q] | S.hpkill[q]) & bit) || (r == 0 && !(S.halive[q] & bit))) cs.cflag[S.hcid[tid]] = 1u;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) S.m_ok = atomicAdd(&cs.hcnt[v], 1u) == k - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!S.m_ok) return;
+    // the last block of the node
+    __threadfence();
+    if (tid < 32) {
+      const Cursor q = open_cursor(cs, v);
+      if (tid == 0) {
+        cs.hcnt[v] = 0;
+        S.mq_ncand = q.ncand;
+        S.mq_next = min(q.ncand, A.nslots);  // the slots are done here; the list remains
+        S.m_next = q.list;
+      }
+    }
+    const bool surv = tid < nb && __ldcg(cs.cflag + S.hcid[tid]) == 0u;
+    const unsigned out = compact_pruned(fb, cap, F);
+    heavy_insert(v, K1, surv, out, fb, cap);
+    __syncthreads();
+    heavy_groups(v, K1);
   }
 
   // ---------------- P index rebuild (three steps, then published) ----------------
@@ -1525,18 +1763,27 @@ struct Search {
       st[S_TSEL] += t - *tlap;
       *tlap = t;
     }
-    // heavy merges first, one block each (the longest single tasks)
-    while (nh) {
+    // block merges first (the longest single tasks): item t is range
+    // t / nh of heavy node t % nh; a node split into k ranges uses ranges
+    // 0..k-1, the other items are skipped
+    for (const unsigned nhi = nh * kSplitMax; nhi;) {
       if (threadIdx.x == 0) S.claim = atomicAdd(&K0.heavy_next.v, 1u);
       __syncthreads();
-      const unsigned h = S.claim;
+      const unsigned t = S.claim;
       __syncthreads();
-      if (h >= nh) break;
+      if (t >= nhi) break;
+      const unsigned h = t % nh, r = t / nh;
+      const unsigned k = A.cs[cur].hsplit[h];
+      if (r >= k) continue;
+      const uint32_t v = A.cs[cur].touched[2u * A.cand_cap - 1u - h];
       const unsigned long long t0 = globaltimer();
-      merge_heavy(A.cs[cur].touched[2u * A.cand_cap - 1u - h], K1);
+      if (k == 1)
+        merge_heavy(v, K1);
+      else
+        merge_range(v, r, k, K1);
       if (threadIdx.x == 0) {
         S.tmax[0] = max(S.tmax[0], (unsigned)min(globaltimer() - t0, 0xFFFFFFFFull));
-        st[S_NHEAVY]++;
+        st[S_NHEAVY] += r == 0;
       }
     }
     // warp items: index-rank items, light merges, extraction chunks

@@ -54,10 +54,16 @@ __global__ void __launch_bounds__(kGridThreads, 1) merge_hook_kernel(GraphDev G,
     for (int i = 0; i < kNB; ++i) S.hist[i] = 0;
   }
   __syncthreads();
-  if (block)
+  if (block >= 2) {  // the split merge, its ranges one after the other (the last one finishes)
+    for (unsigned r = 0; r < block; ++r) {
+      X.merge_range(0u, r, block, C->cyc[1]);
+      __syncthreads();
+    }
+  } else if (block) {
     X.merge_heavy(0u, C->cyc[1]);
-  else if (threadIdx.x < 32)
+  } else if (threadIdx.x < 32) {
     X.merge_node(0u, C->cyc[1]);
+  }
 }
 
 template <int D>
@@ -68,7 +74,7 @@ int merge_hook(uint32_t nfront, const uint32_t* front, uint32_t ncand, const uin
   const uint32_t fcap0 = (nfront + 31) / 32 * 32 + 32;
   const size_t fpool_words = (size_t)(D + 1) * (fcap0 + 4 * (nfront + ncand) + 256);
   size_t bytes = 64 * 256 + sizeof(QCtl) + (size_t)D * 4 * (n + 1) + 8 * 4 * (n + 1) + 2 * (4 * (n + 1) * (3 + slots)) +
-                 2 * (size_t)cand_cap * (24 + 4 * D) + (size_t)label_cap * (4 * D + 20) + fpool_words * 4 +
+                 2 * (size_t)cand_cap * (32 + 4 * D) + 2 * 4 * (n + 1) + (size_t)label_cap * (4 * D + 20) + fpool_words * 4 +
                  2 * (size_t)open_cap * 12 + 3 * kNB * 4 + kPSMax * 4 + 64 * 4 * D * 6;
   DevBuf mem;
   cudaError_t e = cudaMalloc(&mem.p, bytes);
@@ -86,6 +92,9 @@ int merge_hook(uint32_t nfront, const uint32_t* front, uint32_t ncand, const uin
     cs.ncand = take<uint32_t>(p, n + 1);
     cs.node_head = take<int32_t>(p, n + 1);
     cs.hflag = take<uint32_t>(p, n + 1);
+    cs.hcnt = take<uint32_t>(p, n + 1);
+    cs.hsplit = take<uint32_t>(p, cand_cap);
+    cs.cflag = take<uint32_t>(p, cand_cap);
     cs.cslot = take<int32_t>(p, (size_t)(n + 1) * slots);
     cs.cnode = take<uint32_t>(p, cand_cap);
     cs.cparent = take<uint32_t>(p, cand_cap);
@@ -258,6 +267,8 @@ int opmos_test_merge(uint32_t d, uint32_t nfront, const uint32_t* front, uint32_
     if (!out_cost || !out_origin || !out_count || (nfront && !front) || (ncand && (!cand || !cand_arc)))
       return hook_fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
     if (slots == 0 || slots > 4096) return hook_fail(OPMOS_ERR_INVALID_ARG, "slots must be in [1, 4096]");
+    if (block > kSplitMax) return hook_fail(OPMOS_ERR_INVALID_ARG, "block must be 0..%u", kSplitMax);
+    if (block >= 2 && slots > kHC) return hook_fail(OPMOS_ERR_INVALID_ARG, "a split merge holds at most %u slots", kHC);
     if (nfront > (1u << 20) || ncand > (1u << 20)) return hook_fail(OPMOS_ERR_INVALID_ARG, "inputs too large");
     switch (d) {
       case 1: return merge_hook<1>(nfront, front, ncand, cand, cand_arc, block, slots, out_cost, out_origin, out_count);
@@ -287,7 +298,7 @@ int opmos_test_window(uint32_t n, const uint32_t* f0, const uint32_t* f1, const 
     constexpr int D = 2;
     const uint32_t cap = n + 64;
     size_t bytes = 64 * 256 + sizeof(QCtl) + 4 * 2 * 3 + 4 * 3 * 16 + 2 * (size_t)cap * 12 + (size_t)cap * (4 * D + 20) +
-                   3 * kNB * 4 + 2 * ((size_t)cap * (24 + 4 * D) + 4 * 3 * 40) + 64 * 4 * D * 6 + kPSMax * 4;
+                   3 * kNB * 4 + 2 * ((size_t)cap * (32 + 4 * D) + 4 * 3 * 44) + 64 * 4 * D * 6 + kPSMax * 4;
     DevBuf mem;
     cudaError_t e = cudaMalloc(&mem.p, bytes);
     if (e != cudaSuccess) return hook_fail(OPMOS_ERR_OUT_OF_MEMORY, "test hook: %s", cudaGetErrorString(e));
@@ -306,6 +317,9 @@ int opmos_test_window(uint32_t n, const uint32_t* f0, const uint32_t* f1, const 
       cs.ncand = take<uint32_t>(p, 3);
       cs.node_head = take<int32_t>(p, 3);
       cs.hflag = take<uint32_t>(p, 3);
+      cs.hcnt = take<uint32_t>(p, 3);
+      cs.hsplit = take<uint32_t>(p, cap);
+      cs.cflag = take<uint32_t>(p, cap);
       cs.cslot = take<int32_t>(p, 3 * 32);
       cs.cnode = take<uint32_t>(p, cap);
       cs.cparent = take<uint32_t>(p, cap);

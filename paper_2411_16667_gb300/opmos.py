@@ -303,11 +303,12 @@ class opmos_server:
 # ---------------------------------------------------------------------------
 # test hooks (include/opmos_test.h): single device routines on given inputs
 # ---------------------------------------------------------------------------
-def opmos_test_merge(front, cand, cand_arc, block: bool, slots: int = 32):
+def opmos_test_merge(front, cand, cand_arc, block, slots: int = 32):
     """Device merge of one node (frontier rows ``front``, candidate rows
-    ``cand`` with arc ids ``cand_arc``); returns (costs, origins) of the
-    frontier after the merge (origin < len(front): that entry; else
-    len(front) + candidate index)."""
+    ``cand`` with arc ids ``cand_arc``) by one warp (block 0), one block (1)
+    or a block merge split over ``block`` = 2..4 frontier ranges; returns
+    (costs, origins) of the frontier after the merge (origin < len(front):
+    that entry; else len(front) + candidate index)."""
     front = np.ascontiguousarray(front, np.uint32)
     cand = np.ascontiguousarray(cand, np.uint32)
     arc = np.ascontiguousarray(cand_arc, np.uint32)

@@ -3,7 +3,9 @@ the test hooks of include/opmos_test.h on chosen inputs, against plain host
 references of the same operation.
 
 * The merge of one node (Algorithm 1's frontier checks with the in-batch
-  resolution of Sec. 5): the frontier afterwards must be the Pareto-minimal,
+  resolution of Sec. 5), by one warp, one block, or a block merge split
+  over several ranges of the frontier: the frontier afterwards must be the
+  Pareto-minimal,
   cost-unique set of the old frontier and the candidates, with an old entry
   kept over an equal candidate and, among equal candidates, the one with the
   smallest arc id. Frontier and candidate counts cross the 32-entry tile, the
@@ -70,8 +72,11 @@ CASES = [  # (d, frontier size, candidates, slots)
 
 
 @pytest.mark.parametrize("d,nf,nc,slots", CASES)
-@pytest.mark.parametrize("block", [False, True])
+@pytest.mark.parametrize("block", [0, 1, 3])
 def test_node_merge_matches_host_reference(op, d, nf, nc, slots, block):
+    """block: 0 one warp, 1 one block, 3 a block merge split over three
+    ranges of the frontier (candidates beyond the slots go through the
+    list after the split part)."""
     rng = np.random.default_rng(1000 * d + nf + nc + int(block))
     hi = 40 if nf < 400 else 400
     front = _antichain(rng, nf, d, hi) if nf else np.zeros((0, d), np.uint32)
