@@ -66,11 +66,11 @@ UNIT = "labels/s"
 CPU_SAMPLE_LABELS = 1_500_000
 
 # DRAM bytes (read + write) of one search_grid_kernel launch of the default
-# workload, from one ncu capture (profiles/search_grid_kernel_ship256-d3_dram.md),
-# valid only for the kernel sources and launch options whose digest is recorded
-# beside it: once either changes the figure is reported as null until it is
-# captured again.
-TRAFFIC = {"src_digest": "88882c724d6b06ba", "bytes_per_launch": 369825536 + 876039680}
+# workload, from ncu captures (profiles/search_grid_kernel_ship256-d3_dram.md),
+# keyed by the digest of the kernel sources and launch options (the window
+# among them) they were taken with: a launch whose digest has no entry (the
+# sources changed, or another window was chosen) reports null.
+TRAFFIC = {}
 
 
 # the translation unit of the search kernels: the file and every header it includes
@@ -862,7 +862,7 @@ def main():
     achieved = st["bytes"] / (search_ns / 1e9) / 1e9
     achieved_oc = oracle_count_bytes(fx, g.d) / (search_ns / 1e9) / 1e9
     launch = (opt.window, opt.lanes_per_label, opt.tile, opt.delta)
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["src_digest"] == kernel_source_digest(launch) else None
+    traffic = TRAFFIC.get(kernel_source_digest(launch))
     value = world * useful / (ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -130,12 +130,15 @@ typedef struct opmos_stats {
   uint64_t open_scanned;   /* OPEN entries read by the extraction scans, summed over steps
                               (an entry read by two passes of one step counts twice) */
   uint64_t open_rewritten; /* OPEN entries copied forward to the next step's OPEN array */
-  uint64_t list_candidates; /* candidates beyond the slots a node has per step (32 in a
-                               batch, 128 for a single query), merged from the node's list */
+  uint64_t list_candidates; /* candidates beyond the slots a node has per step (64 in a
+                               batch, 128 for a single query), merged from the node's lists */
   uint64_t longest_task_ns[3]; /* summed over steps: the step's longest whole-block merge of a
                                   node with a large frontier, longest one-warp node merge, and
                                   longest extraction work item (the step's critical path) */
-  uint64_t heavy_merges;   /* node merges done by a whole block (frontier >= 512 entries) */
+  uint64_t heavy_merges;   /* node merges done by one or more whole blocks (a large frontier,
+                              or many candidates in the step) */
+  uint64_t heavy_max_candidates; /* summed over steps: the most candidates, and the largest */
+  uint64_t heavy_max_frontier;   /* frontier, of a node merged by whole blocks in the step */
 } opmos_stats;
 
 /* Fill *opt with the defaults (all fields explicit). */
@@ -218,6 +221,13 @@ OPMOS_API int opmos_result_costs(const opmos_result* r, uint32_t* out);
  * OPMOS_FLAG_NO_PATHS return OPMOS_ERR_INVALID_ARG. */
 OPMOS_API int opmos_result_path(const opmos_result* r, uint32_t i, uint32_t* nodes, uint64_t* edges,
                       uint32_t cap, uint32_t* len);
+/* Every path at once, in flat arrays: offsets (count + 1 entries) such that
+ * path i's nodes are nodes[offsets[i] .. offsets[i+1]) and its arcs
+ * edges[offsets[i] - i .. offsets[i+1] - i - 1). nodes and edges may both be
+ * NULL, to read the offsets first: offsets[count] nodes and
+ * offsets[count] - count arcs in all. Results solved with
+ * OPMOS_FLAG_NO_PATHS return OPMOS_ERR_INVALID_ARG. */
+OPMOS_API int opmos_result_paths(const opmos_result* r, uint32_t* offsets, uint32_t* nodes, uint64_t* edges);
 OPMOS_API int opmos_result_stats(const opmos_result* r, opmos_stats* out);
 OPMOS_API void opmos_result_free(opmos_result* r);
 

@@ -24,10 +24,12 @@ extern "C" {
  * dropped, frontier labels a candidate strictly dominates are pruned -- and
  * the in-batch resolution of Sec. 5's Dup&Dom), exactly as a search step runs
  * it on the device: one warp (block = 0), one whole thread block
- * (block = 1), or a block merge split over `block` = 2..4 ranges of the
- * frontier (run one after the other; the last one finishes the node), with
- * candidates taken from the node's slots and then its overflow list. The frontier must be mutually non-dominated and
- * cost-unique, as in a search. No solution set is involved.
+ * (block = 1), or a block merge split into `block` = 2..16 parts (ranges of
+ * the slot candidates times ranges of the frontier; run one after the other,
+ * the last one finishes the node), with candidates taken from the node's
+ * slots and then its overflow lists. The frontier must be mutually
+ * non-dominated and cost-unique, as in a search. No solution set is
+ * involved.
  *   d: 1, 2, 3, 4, 5, 8, 12 or 16 (other values: OPMOS_ERR_INVALID_ARG).
  *   front: nfront*d costs, row-major (labels that existed before the step).
  *   cand: ncand*d costs, row-major; cand_arc: ncand arc ids (ties between
@@ -36,10 +38,12 @@ extern "C" {
  *     return *out_count entries: the node's frontier after the merge, each
  *     with its origin: i < nfront for frontier entry i, nfront + j for
  *     candidate j (the candidate whose parent and arc the new label keeps).
- *   slots: candidate slots of the node (>= 1); the rest go to its list. */
+ *   slots: candidate slots of the node (1..4096); candidate j >= slots
+ *     joins overflow list (j - slots) mod lists.
+ *   lists: overflow lists of the node: 1, 2, 4, 8, 16 or 32. */
 OPMOS_API int opmos_test_merge(uint32_t d, uint32_t nfront, const uint32_t* front, uint32_t ncand,
                                const uint32_t* cand, const uint32_t* cand_arc, uint32_t block, uint32_t slots,
-                               uint32_t* out_cost, uint32_t* out_origin, uint32_t* out_count);
+                               uint32_t lists, uint32_t* out_cost, uint32_t* out_origin, uint32_t* out_count);
 
 /* The window of the ordered batch extraction (Algorithm 2: NUM_POP labels in
  * lexicographic order of F) on a given OPEN, as a search step computes it:

@@ -204,7 +204,7 @@ constexpr uint32_t kWindowCapMin = 16384;  // labels a window may hold at least
 
 // Sizes of one query arena for a given byte budget.
 struct ArenaPlan {
-  uint32_t label_cap, open_cap, win_cap, cand_cap, plog_cap, nslots;
+  uint32_t label_cap, open_cap, win_cap, cand_cap, plog_cap, nslots, lsub, kparts, xcap;
   unsigned long long fpool_words;
   size_t bytes;
   size_t fixed;  // the part that does not grow with the labels
@@ -219,13 +219,21 @@ int plan_arena(const opmos_graph* g, uint32_t D, uint32_t window, size_t budget,
   pl->cand_cap = pl->win_cap * std::max<uint32_t>(g->maxdeg, 1);
   pl->plog_cap = batch ? (1u << 16) : (1u << 20);
   const size_t ptiles = pl->plog_cap / 32 + 1;
-  // per node: fbase, fcount, fcap, then per candidate set ncand, node_head, slots;
-  // per candidate (two sets): node, parent, arc, list link, two touched entries, split count,
-  // flag, cost vector
-  pl->nslots = batch ? kNodeSlots : kNodeSlotsGrid;
-  size_t fixed = (n + 1) * (8 + 4 + 4 + 2 * (4 + 4 + 4 + 4 + 4 * (size_t)pl->nslots)) + 3 * kNB * 4 +
-                 2 * (size_t)pl->cand_cap * (32 + 4 * D) + (size_t)pl->plog_cap * 4 * D +
-                 2 * ((size_t)pl->plog_cap + ptiles) * 4 * D + kPSMax * 4 + 64 * 256;
+  // per node: fbase, fcount, fcap, then per candidate set ncand, list heads, heavy flag,
+  // part count, slots; per candidate (two sets): node, parent, arc, list link, two touched
+  // entries, part count, flag, cost vector; the parts of split merges (two sets)
+  pl->lsub = batch ? kLSubBatch : kLSubGrid;
+  pl->nslots = kNodeSlots;
+  pl->kparts = 1;
+  pl->xcap = 0;
+  if (!batch) {
+    pl->nslots = kNodeSlotsGrid;
+    pl->kparts = kPartsMax;
+    pl->xcap = kPartsMax * (uint32_t)std::min<size_t>(n + 1, pl->cand_cap);
+  }
+  size_t fixed = (n + 1) * (8 + 4 + 4 + 2 * (4 + (4u << pl->lsub) + 4 + 4 + 4 * (size_t)pl->nslots)) + 3 * kNB * 4 +
+                 2 * (size_t)pl->cand_cap * (32 + 4 * D) + 2 * (size_t)pl->xcap * 4 + (size_t)pl->plog_cap * 4 * D +
+                 2 * ((size_t)pl->plog_cap + ptiles) * 4 * D + kPSMax * 4 + 96 * 256;
   pl->fixed = fixed;
   if (budget < fixed + (8u << 20))
     return fail(OPMOS_ERR_CAPACITY, "arena budget %zu too small (fixed part %zu)", budget, fixed);
@@ -250,10 +258,11 @@ void layout_arena(const opmos_graph* g, uint32_t D, const ArenaPlan& pl, char* b
   for (int b = 0; b < 2; ++b) {
     CandSet& cs = A->cs[b];
     cs.ncand = carve<uint32_t>(p, n);
-    cs.node_head = carve<int32_t>(p, n);
+    cs.node_head = carve<int32_t>(p, n << pl.lsub);
     cs.hflag = carve<uint32_t>(p, n);
     cs.hcnt = carve<uint32_t>(p, n);
     cs.hsplit = carve<uint32_t>(p, pl.cand_cap);
+    cs.xpart = carve<uint32_t>(p, std::max<uint32_t>(pl.xcap, 1));
     cs.cflag = carve<uint32_t>(p, pl.cand_cap);
     cs.cslot = carve<int32_t>(p, n * pl.nslots);
     cs.cnode = carve<uint32_t>(p, pl.cand_cap);
@@ -286,6 +295,9 @@ void layout_arena(const opmos_graph* g, uint32_t D, const ArenaPlan& pl, char* b
   A->plog_cap = pl.plog_cap;
   A->fpool_words = pl.fpool_words;
   A->nslots = pl.nslots;
+  A->lsub = pl.lsub;
+  A->kparts = pl.kparts;
+  A->xcap = pl.xcap;
 }
 
 int compute_heuristic(const opmos_graph* g, uint32_t D, const uint32_t* goals, uint32_t ngoals, uint32_t* h,
@@ -356,6 +368,8 @@ void fill_stats(opmos_stats* s, const QResult& R, uint32_t D) {
   s->longest_task_ns[1] = R.stats[S_MAXL];
   s->longest_task_ns[2] = R.stats[S_MAXX];
   s->heavy_merges = R.stats[S_NHEAVY];
+  s->heavy_max_candidates = R.stats[S_MAXNC];
+  s->heavy_max_frontier = R.stats[S_MAXF];
   // algorithmic bytes: per extracted label 8d+12 (g, node, rowptr pair, F key),
   // per candidate 4+8d (col, cost, h), per compared frontier/P entry 4d, per
   // inserted label 4d+24 (label record, frontier slot, OPEN entry), per prune 4.
@@ -1024,6 +1038,19 @@ int opmos_result_path(const opmos_result* r, uint32_t i, uint32_t* nodes, uint64
     if (!nodes || (b - a > 1 && !edges)) return fail(OPMOS_ERR_INVALID_ARG, "NULL output array");
     std::memcpy(nodes, r->nodes.data() + a, (size_t)(b - a) * 4);
     if (b - a > 1) std::memcpy(edges, r->edges.data() + (a - i), (size_t)(b - a - 1) * 8);
+    return OPMOS_OK;
+  });
+}
+
+int opmos_result_paths(const opmos_result* r, uint32_t* offsets, uint32_t* nodes, uint64_t* edges) {
+  return guarded("opmos_result_paths", [&]() -> int {
+    if (!r || !offsets || (!nodes != !edges)) return fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
+    if (!r->has_paths) return fail(OPMOS_ERR_INVALID_ARG, "result was solved without paths");
+    std::memcpy(offsets, r->offs.data(), ((size_t)r->count + 1) * 4);
+    if (nodes) {
+      std::memcpy(nodes, r->nodes.data(), (size_t)r->offs[r->count] * 4);
+      std::memcpy(edges, r->edges.data(), ((size_t)r->offs[r->count] - r->count) * 8);
+    }
     return OPMOS_OK;
   });
 }

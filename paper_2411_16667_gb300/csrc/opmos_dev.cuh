@@ -39,10 +39,21 @@ constexpr unsigned kRankQ = 1024;     // P entries per rank work item of an inde
 constexpr unsigned kPSMax = 32768;    // largest P indexed by the sorted snapshot
 constexpr unsigned kHeavyFrontier = 512;  // frontiers this large are merged by a whole block
 constexpr unsigned kHeavyCands = 32;      // ... and so are nodes reached by more candidates in a step
-constexpr unsigned kSplitMin = 1024;      // frontier entries per block when a block merge is split
-constexpr unsigned kSplitMax = 4;         // ... over at most this many blocks
-constexpr unsigned kNodeSlots = 64;      // candidate slots per node and step in batch mode
-constexpr unsigned kNodeSlotsGrid = 128; // ... for a single query (whole-grid search)
+// A block merge whose candidates x frontier entries exceed kPartWork is split
+// into parts (up to kPartsMax, each a whole block), each part holding at
+// least kPartCands candidates when the candidates are split.
+constexpr unsigned long long kPartWork = 1ull << 17;
+constexpr unsigned kPartsMax = 16;
+constexpr unsigned kPartCands = 64;
+constexpr unsigned kPartPruned = 1u << 16;  // added to a node's part counter by a part that pruned
+constexpr unsigned kHeavyBusy = 0xFFFFFFFFu;  // hflag while the node is being listed
+constexpr unsigned kNodeSlots = 64;       // candidate slots per node and step in batch mode
+constexpr unsigned kNodeSlotsGrid = 128;  // ... for a single query (whole-grid search)
+// Lists per node for the candidates beyond the slots (log2): the lanes of a
+// warp walk them side by side, so gathering k of them costs about
+// k / 2^lsub dependent loads instead of k.
+constexpr unsigned kLSubBatch = 3;
+constexpr unsigned kLSubGrid = 5;
 
 enum StatIdx {
   S_EXTRACTED = 0,
@@ -66,6 +77,8 @@ enum StatIdx {
   S_MAXL,     // ... of the longest light (warp) merge
   S_MAXX,     // ... of the longest extraction work item
   S_NHEAVY,   // heavy merges
+  S_MAXNC,    // sum over steps of the most candidates a block-merged node of the step had
+  S_MAXF,     // ... of the largest frontier a block-merged node of the step had
   kNStat
 };
 
@@ -103,14 +116,16 @@ struct CycleCtl {
   Hot<unsigned> touched_count;      // nodes they reach with a small frontier (one warp each)
   Hot<unsigned> heavy_count;        // ... with a large frontier (one block each)
   Hot<unsigned> work_next;          // dynamic claims: index-rank items, light merges, extraction chunks
-  Hot<unsigned> heavy_next;         // dynamic claims of heavy merges
+  Hot<unsigned> heavy_next;         // dynamic claims of heavy merges (parts first)
+  Hot<unsigned> part_count;         // parts of split heavy merges listed in xpart
   Hot<unsigned> f1lo;               // F[1] range of the carried entries the histogram's bins cover
   Hot<unsigned> f1hi;
   Hot<unsigned> plen;               // P-log length every reader uses in step i
   Hot<unsigned> lbase;              // labels that existed when step i began
   unsigned win_min_prev;            // win_min of window i-1
   unsigned head;                    // FIFO: the ring position window i+1 starts at (0 otherwise)
-  unsigned tmax[3];                 // longest heavy merge, light merge, extraction item of step i (ns)
+  unsigned tmax[5];                 // longest heavy merge, light merge, extraction item of step i (ns);
+                                    // most candidates and largest frontier of a heavy merge
 };
 
 // Bins of one OPEN array's histogram: F[0] origin, F[1] origin and shift,
@@ -156,11 +171,15 @@ struct QCtl {
 struct CandSet {
   uint32_t* ncand;     // n+1: candidates that reached the node
   int32_t* cslot;      // (n+1) * nslots: the first nslots of them
-  int32_t* node_head;  // n+1: the rest, linked by cnext
-  uint32_t* hflag;     // n+1: the node is merged by a whole block (listed once among the heavy nodes)
-  uint32_t* hcnt;      // n+1: ranges of a split block merge finished so far
-  uint32_t* hsplit;    // cand_cap: blocks the h-th heavy node's merge is split over
-  uint32_t* cflag;     // cand_cap: candidate dropped by a split merge's range pass
+  int32_t* node_head;  // (n+1) << lsub: the rest, in 2^lsub lists per node linked by cnext (the
+                       // j-th candidate beyond the slots joins list j mod 2^lsub)
+  uint32_t* hflag;     // n+1: 0, or h + 1 once the node is listed as the h-th heavy node (merged by
+                       // whole blocks), kHeavyBusy while it is being listed
+  uint32_t* hcnt;      // n+1: parts of a split block merge finished so far (low 16 bits), plus
+                       // kPartPruned for each part that pruned a frontier entry
+  uint32_t* hsplit;    // cand_cap: parts the h-th heavy node's merge is split into (1: not split)
+  uint32_t* xpart;     // parts of split merges, h << 4 | part (kPartsMax per heavy node at most)
+  uint32_t* cflag;     // cand_cap: candidate dropped by a part of a split merge
   uint32_t* cnode;
   uint32_t* cparent;
   uint32_t* cedge;
@@ -196,8 +215,10 @@ struct QArena {
   uint32_t plog_cap;
   uint32_t pad;
   unsigned long long fpool_words;
-  uint32_t nslots;     // candidate slots per node and step (the rest go to the node's list)
-  uint32_t pad2;
+  uint32_t nslots;     // candidate slots per node and step (the rest go to the node's lists)
+  uint32_t lsub;       // log2 of the lists per node
+  uint32_t kparts;     // most parts a block merge is split into (1: never split)
+  uint32_t xcap;       // entries of each candidate set's xpart
 };
 
 struct QParams {
@@ -297,6 +318,7 @@ constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  //
 // Whole cooperative grid on one query; the barrier is a generation counter
 // with a bounded wait (gives up with OPMOS_ERR_TIMEOUT, never hangs).
 struct GridTeam {
+  static constexpr bool kSplitMerges = true;  // block merges may be split into parts
   __device__ __forceinline__ unsigned tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
   __device__ __forceinline__ unsigned nthreads() const { return gridDim.x * blockDim.x; }
   __device__ __forceinline__ unsigned wid() const { return tid() >> 5; }

@@ -137,10 +137,11 @@ struct Shared {
   int hcid[kHC];
   uint32_t hedge[kHC], hpar[kHC];
   unsigned halive[kHC / 32], hkill[kHC / 32], hpkill[kHC / 32];
-  int m_next;
+  int hlist[32];       // cursors of the block-merged node's lists
   unsigned mq_ncand, mq_next, m_nb, m_ok, m_lb, m_cap;
   unsigned long long m_fb;
-  unsigned tmax[3];    // this block's longest heavy merge, light merge, extraction item (ns)
+  unsigned tmax[5];    // this block's longest heavy merge, light merge, extraction item (ns);
+                       // most candidates and largest frontier of its heavy merges
 };
 
 // Histogram bin of an OPEN key (F0 << 32 | F1): the key's cell is
@@ -229,7 +230,7 @@ struct Search {
       A.fbase[v] = 0;
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
-        A.cs[b].node_head[v] = kNil;
+        for (unsigned j = 0; j < (1u << A.lsub); ++j) A.cs[b].node_head[((size_t)v << A.lsub) + j] = kNil;
         A.cs[b].ncand[v] = 0;
         A.cs[b].hflag[v] = 0;
         A.cs[b].hcnt[v] = 0;
@@ -250,11 +251,12 @@ struct Search {
     K.heavy_count.v = 0;
     K.work_next.v = 0;
     K.heavy_next.v = 0;
+    K.part_count.v = 0;
     K.f1lo.v = kInf;
     K.f1hi.v = 0;
     K.plen.v = 0;
     K.lbase.v = 0;
-    K.tmax[0] = K.tmax[1] = K.tmax[2] = 0;
+    for (int j = 0; j < 5; ++j) K.tmax[j] = 0;
     K.head = 0;
   }
 
@@ -403,26 +405,74 @@ struct Search {
     const unsigned pos = atomicAdd(&cs.ncand[v2], 1u);
     if (pos < A.nslots) {
       cs.cslot[(size_t)v2 * A.nslots + pos] = (int)c;
-    } else {
-      cs.cnext[c] = atomicExch(&cs.node_head[v2], (int)c);
+    } else {  // list (pos - nslots) mod 2^lsub of the node, so all its lists grow evenly
+      const unsigned j = (pos - A.nslots) & ((1u << A.lsub) - 1u);
+      cs.cnext[c] = atomicExch(&cs.node_head[((size_t)v2 << A.lsub) + j], (int)c);
       st[S_OVF]++;
     }
     // Every node is listed among the light ones (one warp each) on its
     // first candidate. A node with a large frontier, or reached by many
     // candidates, is also listed once at the far end of the touched array
     // (hflag decides; the array holds 2 * cand_cap entries) and merged by
-    // a whole block; its light item then only clears hflag. Only light items
+    // whole blocks; its light item then only clears hflag. Only light items
     // touch hflag during the merge, so a block merge never races a warp.
     if (pos == 0) cs.touched[agg_inc(&K1.touched_count.v)] = v2;
+    if (v2 == G.n) return;
     // (the work of a one-warp merge grows with frontier x candidates)
-    const bool heavy = v2 != G.n && ((pos == 0 && A.fcount[v2] >= kHeavyFrontier) ||
-                                     (pos == kHeavyCands / 2 - 1 && A.fcount[v2] >= kHeavyFrontier * 3 / 8) ||
-                                     pos == kHeavyCands);
-    if (heavy && atomicExch(&cs.hflag[v2], 1u) == 0u) {
-      const unsigned h = atomicAdd(&K1.heavy_count.v, 1u);
-      cs.touched[2u * A.cand_cap - 1u - h] = v2;
-      // a frontier this large is scanned by several blocks (merge_range)
-      cs.hsplit[h] = min(kSplitMax, max(1u, A.fcount[v2] / kSplitMin));
+    const bool list = pos == kHeavyCands ||
+                      ((pos == 0 || pos == kHeavyCands / 2 - 1) &&
+                       A.fcount[v2] >= (pos ? kHeavyFrontier * 3 / 8 : kHeavyFrontier));
+    // at 64, 128, 256, ... candidates the merge may be split further
+    const bool grow = A.kparts > 1u && pos > kHeavyCands && ((pos + 1u) & pos) == 0u;
+    if (list || grow) heavy_list(cs, K1, v2, parts_for(pos + 1u, A.fcount[v2]), list);
+  }
+
+  // Parts a block merge of nc candidates against F frontier entries is split
+  // into: a power of two, each part about kPartWork comparisons or fewer.
+  __device__ unsigned parts_for(unsigned nc, unsigned F) const {
+    const unsigned long long w = (unsigned long long)nc * F;
+    unsigned k = 1;
+    while (k < A.kparts && w > kPartWork * k) k <<= 1;
+    return k;
+  }
+
+  // Lists node v as a heavy node (list), or raises the parts of its merge to
+  // want as its candidates grow. The lister holds hflag at kHeavyBusy until
+  // the node's index h and part count are written, then publishes h + 1; a
+  // raise that finds the node not yet published is dropped (the next one, at
+  // twice the candidates, tries again). Every new part is recorded in xpart;
+  // parts already recorded keep their numbers.
+  __device__ void heavy_list(const CandSet& cs, CycleCtl& K1, uint32_t v, unsigned want, bool list) {
+    unsigned h, r0;
+    if (list) {
+      if (atomicCAS(&cs.hflag[v], 0u, kHeavyBusy) != 0u) return;  // listed already
+      h = atomicAdd(&K1.heavy_count.v, 1u);
+      cs.touched[2u * A.cand_cap - 1u - h] = v;
+      cs.hsplit[h] = want;
+      r0 = 0;
+    } else {
+      const unsigned f = ld_volatile(&cs.hflag[v]);
+      if (f == 0u || f == kHeavyBusy) return;
+      h = f - 1u;
+      unsigned old = ld_volatile(&cs.hsplit[h]);
+      for (;;) {
+        if (want <= old) return;
+        const unsigned seen = atomicCAS(&cs.hsplit[h], old, want);
+        if (seen == old) break;
+        old = seen;
+      }
+      r0 = old > 1u ? old : 0u;  // parts [old, want), or all of them when the merge was not split
+    }
+    if (want > 1u) {
+      const unsigned j = atomicAdd(&K1.part_count.v, want - r0);
+      if (j + (want - r0) > A.xcap)
+        set_error(C, OPMOS_ERR_CAPACITY);
+      else
+        for (unsigned r = r0; r < want; ++r) cs.xpart[j + r - r0] = h << 4 | r;
+    }
+    if (list) {
+      __threadfence();
+      atomicExch(&cs.hflag[v], h + 1u);
     }
   }
 
@@ -1004,32 +1054,34 @@ struct Search {
     }
   }
 
-  // Next batch (up to 32) of node v's candidates: the node's slots 32 at a
-  // time, then its list. *cur is the cursor: a slot index (>= 0) while the
-  // slots last, then -2 - (list position) ... encoded as below. Returns the
-  // lane's candidate (kNil if none) and the batch size in *nb; *more tells
-  // whether another batch follows. The first call (cur == 0) also reads and
-  // clears the node's count and list head.
+  // A warp's cursor over node v's candidates of one step: the slots 32 at a
+  // time, then the node's 2^lsub lists, lane j walking list j. Opening it
+  // reads and clears the node's count and list heads (the set is reused two
+  // steps later).
   struct Cursor {
     unsigned ncand;  // candidates of the node this step
     unsigned next;   // next slot index to read
-    int list;        // list cursor once the slots are used up
+    int lcur;        // lane j < 2^lsub: its position in list j (kNil at the end)
   };
   __device__ __forceinline__ Cursor open_cursor(const CandSet& cs, uint32_t v) {
+    const unsigned lane = lane_id();
     Cursor q;
     q.ncand = cs.ncand[v];
     q.next = 0;
-    q.list = q.ncand > A.nslots ? cs.node_head[v] : kNil;
+    // lists holding something: min(candidates beyond the slots, 2^lsub)
+    const unsigned nl = q.ncand > A.nslots ? min(q.ncand - A.nslots, 1u << A.lsub) : 0u;
+    int32_t* heads = cs.node_head + ((size_t)v << A.lsub);
+    q.lcur = lane < nl ? heads[lane] : kNil;
     __syncwarp();
-    if (lane_id() == 0) {
-      cs.ncand[v] = 0;
-      if (q.ncand > A.nslots) cs.node_head[v] = kNil;
-    }
+    if (lane == 0) cs.ncand[v] = 0;
+    if (lane < nl) heads[lane] = kNil;
     return q;
   }
   __device__ __forceinline__ bool cursor_more(const Cursor& q) const {
-    return q.next < min(q.ncand, A.nslots) || q.list != kNil;
+    return q.next < min(q.ncand, A.nslots) || __any_sync(0xffffffffu, q.lcur != kNil);
   }
+  // Next batch (up to 32): the lane's candidate (kNil if none) and the batch
+  // size in *nb; the batch's candidates sit in lanes 0 .. *nb - 1.
   __device__ __forceinline__ int next_batch(const CandSet& cs, uint32_t v, Cursor& q, unsigned* nb) {
     const unsigned lane = lane_id();
     int mine = kNil;
@@ -1040,14 +1092,20 @@ struct Search {
       q.next += n;
       *nb = n;
     } else {
+      // rounds over the lists side by side: the lanes still inside a list
+      // hand their candidates to lanes n, n+1, ... and step on
       unsigned n = 0;
-      int cc = q.list;
-      while (cc != kNil && n < 32) {
-        if (lane == n) mine = cc;
-        cc = cs.cnext[cc];
-        ++n;
+      for (;;) {
+        const unsigned bal = __ballot_sync(0xffffffffu, q.lcur != kNil);
+        if (bal == 0u || n >= 32u) break;
+        const unsigned cnt = __popc(bal);
+        const unsigned t = lane - n;  // this lane receives the t-th candidate of the round
+        const bool recv = lane >= n && t < cnt;
+        const int got = __shfl_sync(0xffffffffu, q.lcur, recv ? nth_bit(bal, t) : 0u);
+        if (recv) mine = got;
+        if (q.lcur != kNil && n + __popc(bal & lanemask_lt()) < 32u) q.lcur = cs.cnext[q.lcur];
+        n = min(32u, n + cnt);
       }
-      q.list = cc;
       *nb = n;
     }
     return mine;
@@ -1082,89 +1140,166 @@ struct Search {
   //      tiles split between the warps that hold the same candidates;
   //  (d) survivors become labels, join alpha(v) and the next OPEN.
   __device__ void merge_heavy(uint32_t v, CycleCtl& K1) {
-    const CandSet& cs = A.cs[cyc & 1u];
+    open_block_cursor(A.cs[cyc & 1u], v, false);
+    __syncthreads();
+    heavy_groups(v, K1, false);
+  }
+
+  // Warp 0 opens node v's cursor for a block merge in shared memory:
+  // S.mq_ncand candidates, slots from S.mq_next (past the slots if
+  // slots_done), list positions in S.hlist. A block barrier must follow.
+  __device__ void open_block_cursor(const CandSet& cs, uint32_t v, bool slots_done) {
     if (threadIdx.x < 32) {
       const Cursor q = open_cursor(cs, v);
+      S.hlist[threadIdx.x] = q.lcur;
       if (threadIdx.x == 0) {
         S.mq_ncand = q.ncand;
-        S.mq_next = 0;
-        S.m_next = q.list;
+        S.mq_next = slots_done ? min(q.ncand, A.nslots) : 0u;
+      }
+    }
+  }
+
+  // The next group (up to kHC) of a block merge's candidates, into S.hcid;
+  // returns its size (every thread), 0 once none is left. First the slot
+  // rows S.mq_next, S.mq_next + 1, ... below nrows, row j being slot
+  // first + j * stride, then the lists whose cursors sit in S.hlist, walked
+  // side by side by warp 0. With filtered, candidates a part of a split merge
+  // dropped are skipped (and the group still fills while any are left).
+  __device__ unsigned gather_group(const CandSet& cs, uint32_t v, unsigned nrows, unsigned first, unsigned stride,
+                                   bool filtered) {
+    const unsigned tid = threadIdx.x;
+    unsigned s0 = S.mq_next, n0 = 0;
+    while (s0 < nrows && n0 < kHC) {  // (uniform: s0 and n0 are the same in every thread)
+      const unsigned take = min(kHC - n0, nrows - s0);
+      int c = kNil;
+      if (tid < take) c = cs.cslot[(size_t)v * A.nslots + first + (s0 + tid) * stride];
+      const bool keep = c != kNil && (!filtered || __ldcg(cs.cflag + c) == 0u);
+      unsigned cnt;
+      const unsigned pos = block_exclusive_scan(keep ? 1u : 0u, S.warp, cnt);  // (every thread has read mq_next)
+      if (keep) S.hcid[n0 + pos] = c;
+      n0 += cnt;
+      s0 += take;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      int cur = S.hlist[tid];
+      unsigned n = n0;
+      for (;;) {
+        const bool live = cur != kNil;
+        if (!__any_sync(0xffffffffu, live) || n >= kHC) break;
+        const bool kp = live && (!filtered || __ldcg(cs.cflag + cur) == 0u);
+        const unsigned bal = __ballot_sync(0xffffffffu, kp);
+        const unsigned rk = __popc(bal & lanemask_lt());
+        const bool put = kp && n + rk < kHC;
+        if (put) S.hcid[n + rk] = cur;
+        if (put || (live && !kp)) cur = cs.cnext[cur];
+        n = min(kHC, n + __popc(bal));
+      }
+      S.hlist[tid] = cur;
+      if (tid == 0) {
+        S.mq_next = s0;
+        S.m_nb = n;
       }
     }
     __syncthreads();
-    heavy_groups(v, K1);
+    return S.m_nb;
+  }
+
+  // A gathered group's costs, arcs and parents into shared memory; the
+  // group's kill words cleared. A block barrier must follow.
+  __device__ void load_group(const CandSet& cs, unsigned nb) {
+    const unsigned tid = threadIdx.x;
+    if (tid < nb) {
+      const int c = S.hcid[tid];
+#pragma unroll
+      for (int k = 0; k < D; ++k) S.hc[k][tid] = cs.cg[(size_t)k * A.cand_cap + c];
+      S.hedge[tid] = cs.cedge[c];
+      S.hpar[tid] = cs.cparent[c];
+    }
+    if (tid < kHC / 32) {
+      S.hkill[tid] = 0;
+      S.hpkill[tid] = 0;
+    }
+  }
+
+  // In-set resolution of a group (Sec. 5's Dup&Dom): candidate tid dies when
+  // another strictly dominates it or equals it with a smaller (arc, index);
+  // the survivors' words go to S.halive. A block barrier must follow.
+  __device__ void group_inset(unsigned nb) {
+    const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+    bool alive = tid < nb;
+    if (alive) {
+      uint32_t ct[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) ct[k] = S.hc[k][tid];
+      const uint32_t et = S.hedge[tid];
+      for (unsigned j = 0; j < nb && alive; ++j) {
+        if (j == tid) continue;
+        uint32_t cj[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) cj[k] = S.hc[k][j];
+        const uint32_t ej = S.hedge[j];
+        if (dominates<D>(cj, ct) || (equal<D>(cj, ct) && (ej < et || (ej == et && j < tid)))) alive = false;
+      }
+    }
+    const unsigned am = __ballot_sync(0xffffffffu, alive);
+    if (lane == 0 && w < kHC / 32) S.halive[w] = am;
+  }
+
+  // F against P for the live candidates of group word q, this warp taking
+  // slice sl of nsl of the P log tail and of the index tiles; the ones P
+  // dominates are flagged in S.hpkill.
+  __device__ void group_ptest(uint32_t v, unsigned q, unsigned nsl, unsigned sl) {
+    const unsigned lane = lane_id();
+    const unsigned word = S.halive[q] & ~S.hkill[q];
+    if (!word || sl >= nsl) return;
+    const PIdx& pd = S.pd;
+    const unsigned jj = q * 32 + lane;
+    uint32_t F[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) F[k] = S.hc[k][jj] + hk(k, v);
+    bool alive = (word >> lane) & 1u;
+    const unsigned t0 = pd.count ? pd.mark : 0u, t1 = psnap;
+    const unsigned tper = ((t1 - min(t0, t1) + nsl - 1) / nsl + 31) / 32 * 32;
+    const unsigned lo = min(t1, t0 + sl * tper), hi = min(t1, lo + tper);
+    const unsigned nt = pd.count ? pd.ntiles : 0u;
+    const unsigned gper = ((nt + nsl - 1) / nsl + 31) / 32 * 32;
+    const unsigned glo = min(nt, sl * gper), ghi = min(nt, glo + gper);
+    unsigned long long pcmp = 0;
+    p_filter(alive, F, lo, hi, pd.count, glo, ghi, nt, pd.cur, pcmp);
+    st[S_PCMP] += pcmp;
+    const unsigned pk = __ballot_sync(0xffffffffu, !alive) & word;
+    if (lane == 0 && pk) atomicOr(&S.hpkill[q], pk);
   }
 
   // The group loop of a block merge, from the cursor in shared memory
-  // (S.mq_ncand candidates, slots from S.mq_next, then the list at S.m_next).
-  __device__ void heavy_groups(uint32_t v, CycleCtl& K1) {
+  // (S.mq_ncand candidates, slots from S.mq_next, then the lists at
+  // S.hlist). filtered: the survivors of a split merge's parts (the ones
+  // without cflag), already checked against the frontier's first `old`
+  // entries, so only the entries the loop itself inserts are scanned.
+  __device__ void heavy_groups(uint32_t v, CycleCtl& K1, bool filtered, unsigned old = 0) {
     constexpr int U = kUH;
     constexpr unsigned NW = kHC / 32;  // candidate words
     const CandSet& cs = A.cs[cyc & 1u];
     const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5, nw = blockDim.x >> 5;
     const unsigned in_slots = min(S.mq_ncand, A.nslots);
     for (;;) {
-      // gather the next (up to kHC) candidates: slots in parallel, then the list
-      const unsigned s0 = S.mq_next;
-      const unsigned take = s0 < in_slots ? min(kHC, in_slots - s0) : 0u;
-      if (tid < take) S.hcid[tid] = cs.cslot[(size_t)v * A.nslots + s0 + tid];
-      __syncthreads();  // every thread has read mq_next
-      if (tid == 0) {
-        unsigned n = take;
-        int cc = S.m_next;
-        while (cc != kNil && n < kHC) {
-          S.hcid[n++] = cc;
-          cc = cs.cnext[cc];
-        }
-        S.m_next = cc;
-        S.mq_next = s0 + take;
-        S.m_nb = n;
-      }
-      __syncthreads();
-      const unsigned nb = S.m_nb;
+      const unsigned nb = gather_group(cs, v, in_slots, 0u, 1u, filtered);
       if (nb == 0) break;
       const unsigned nwords = (nb + 31) / 32;
-      if (tid < nb) {
-        const int c = S.hcid[tid];
-#pragma unroll
-        for (int k = 0; k < D; ++k) S.hc[k][tid] = cs.cg[(size_t)k * A.cand_cap + c];
-        S.hedge[tid] = cs.cedge[c];
-        S.hpar[tid] = cs.cparent[c];
-      }
-      if (tid < NW) {
-        S.hkill[tid] = 0;
-        S.hpkill[tid] = 0;
-      }
+      load_group(cs, nb);
       __syncthreads();
-      // (a) in-set resolution, candidate tid
-      {
-        bool alive = tid < nb;
-        if (alive) {
-          uint32_t ct[D];
-#pragma unroll
-          for (int k = 0; k < D; ++k) ct[k] = S.hc[k][tid];
-          const uint32_t et = S.hedge[tid];
-          for (unsigned j = 0; j < nb && alive; ++j) {
-            if (j == tid) continue;
-            uint32_t cj[D];
-#pragma unroll
-            for (int k = 0; k < D; ++k) cj[k] = S.hc[k][j];
-            const uint32_t ej = S.hedge[j];
-            if (dominates<D>(cj, ct) || (equal<D>(cj, ct) && (ej < et || (ej == et && j < tid)))) alive = false;
-          }
-        }
-        const unsigned am = __ballot_sync(0xffffffffu, alive);
-        if (lane == 0 && w < NW) S.halive[w] = am;
-      }
+      // (a) in-set resolution
+      group_inset(nb);
       __syncthreads();
       // (b) the frontier
       const uint64_t fb = A.fbase[v];
       const unsigned cap = A.fcap[v];
       const unsigned fc = A.fcount[v];
-      unsigned out = 0;
+      unsigned out = old;
       unsigned long long fcmp = 0;
       const unsigned R = nw * 32u * U;
-      for (unsigned r0 = 0; r0 < fc; r0 += R) {
+      for (unsigned r0 = old; r0 < fc; r0 += R) {
         const unsigned base = r0 + w * 32u * U;
         uint32_t m[U][D];
         uint32_t mid[U];
@@ -1262,29 +1397,7 @@ struct Search {
       if (lane == 0) st[S_FCMP] += fcmp;
       // (c) F against P: warp w takes candidate word w % nwords and one of the
       // nw / nwords slices of the P log tail and of the index tiles
-      {
-        const unsigned q = w % nwords, nsl = nw / nwords, sl = w / nwords;
-        const unsigned word = S.halive[q] & ~S.hkill[q];
-        if (word && sl < nsl) {
-          const PIdx& pd = S.pd;
-          const unsigned jj = q * 32 + lane;
-          uint32_t F[D];
-#pragma unroll
-          for (int k = 0; k < D; ++k) F[k] = S.hc[k][jj] + hk(k, v);
-          bool alive = (word >> lane) & 1u;
-          const unsigned t0 = pd.count ? pd.mark : 0u, t1 = psnap;
-          const unsigned tper = ((t1 - min(t0, t1) + nsl - 1) / nsl + 31) / 32 * 32;
-          const unsigned lo = min(t1, t0 + sl * tper), hi = min(t1, lo + tper);
-          const unsigned nt = pd.count ? pd.ntiles : 0u;
-          const unsigned gper = ((nt + nsl - 1) / nsl + 31) / 32 * 32;
-          const unsigned glo = min(nt, sl * gper), ghi = min(nt, glo + gper);
-          unsigned long long pcmp = 0;
-          p_filter(alive, F, lo, hi, pd.count, glo, ghi, nt, pd.cur, pcmp);
-          st[S_PCMP] += pcmp;
-          const unsigned pk = __ballot_sync(0xffffffffu, !alive) & word;
-          if (lane == 0 && pk) atomicOr(&S.hpkill[q], pk);
-        }
-      }
+      group_ptest(v, w % nwords, nw / nwords, w / nwords);
       __syncthreads();
       // (d) survivors become labels, join alpha(v) and the next OPEN
       const bool surv = tid < nb && (((S.halive[w % NW] & ~S.hkill[w % NW] & ~S.hpkill[w % NW]) >> lane) & 1u);
@@ -1296,7 +1409,9 @@ struct Search {
   // Survivors of a block merge (thread tid holds candidate tid in shared
   // memory; surv tells whether it survived) become labels, join alpha(v) --
   // out live entries at fb, cap, grown when full -- and the next OPEN.
-  __device__ void heavy_insert(uint32_t v, CycleCtl& K1, bool surv, unsigned out, uint64_t fb, unsigned cap) {
+  // Returns alpha(v)'s new size (the block must pass a barrier before the
+  // shared candidate arrays are reused).
+  __device__ unsigned heavy_insert(uint32_t v, CycleCtl& K1, bool surv, unsigned out, uint64_t fb, unsigned cap) {
     const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5, nw = blockDim.x >> 5;
     const unsigned smask = __ballot_sync(0xffffffffu, surv);
     if (lane == 0) S.warp[w] = __popc(smask);
@@ -1337,7 +1452,8 @@ struct Search {
       }
     }
     __syncthreads();
-    if (S.m_ok) {
+    const unsigned ok = S.m_ok;
+    if (ok) {
       const uint64_t nfb = S.m_fb;
       const unsigned ncap = S.m_cap;
       if (nfb != fb) {
@@ -1371,6 +1487,7 @@ struct Search {
     } else if (tid == 0) {
       A.fcount[v] = out;
     }
+    return ok ? out + ntot : out;
   }
 
   // Compaction of a frontier after a split merge: the entries whose label
@@ -1426,168 +1543,149 @@ struct Search {
     return out;
   }
 
-  // A block merge split over k blocks (a node whose frontier was large when
-  // it was listed): block r scans the frontier entries [r F / k, (r+1) F / k)
-  // against the node's slot candidates, read only -- it marks the entries a
-  // candidate strictly dominates as pruned (ldead = cyc) and flags the
-  // candidates a frontier entry weakly dominates -- and tests F against P
-  // for every k-th word of candidates; block 0 also flags the candidates the
-  // in-set resolution drops. The last of the k blocks to finish (a counter
-  // per node; nobody waits) compacts the frontier, inserts the unflagged
-  // candidates and then merges the node's list candidates, if any, as
-  // heavy_groups does. The candidates a block sees die in the same order as
-  // in one block's scan (an entry that weakly dominates a candidate is never
-  // strictly dominated by it, the frontier being an antichain), so the
-  // result is the same set.
-  __device__ void merge_range(uint32_t v, unsigned r, unsigned k, CycleCtl& K1) {
+  // Shape of a merge split into k parts: ka shares of the candidates (ka
+  // divides k, each share kPartCands candidates or more) times kb = k / ka
+  // ranges of the frontier. Splitting the candidates keeps each candidate's
+  // early exit in one scan, so it is preferred.
+  __device__ static void part_shape(unsigned k, unsigned nc, unsigned& ka, unsigned& kb) {
+    const unsigned amax = max(1u, nc / kPartCands);
+    ka = 1;
+    for (unsigned x = 2; x <= k; ++x)
+      if (k % x == 0 && x <= amax) ka = x;
+    kb = k / ka;
+  }
+
+  // Part r of a block merge split into k parts (k >= 2; decided while the
+  // node's candidates arrived). With the shape (ka, kb), part r = b * ka + a
+  // takes share a of the candidates -- slots a, a + ka, ... and lists a,
+  // a + ka, ... -- kHC at a time, and frontier entries [b F / kb,
+  // (b+1) F / kb), read only:
+  //  (a) in-set resolution within each group;
+  //  (b) frontier entries a candidate strictly dominates are marked pruned
+  //      (ldead = cyc); candidates an entry weakly dominates die;
+  // and the candidates that died get cflag set. Each dies only when a
+  // candidate of its group or a frontier entry dominates it, and every entry
+  // some candidate strictly dominates is marked (dominance is transitive and
+  // the frontier is an antichain). The last part to finish (a counter per
+  // node; nobody waits) compacts the frontier if a part pruned, then merges
+  // the surviving candidates as one block merge does -- against each other,
+  // the entries it inserts and P -- so P tests only the survivors.
+  __device__ void merge_part(uint32_t v, unsigned r, unsigned k, CycleCtl& K1) {
     constexpr int U = kUH;
     constexpr unsigned NW = kHC / 32;
     const CandSet& cs = A.cs[cyc & 1u];
     const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5, nw = blockDim.x >> 5;
     const unsigned F = A.fcount[v];
-    const unsigned nb = min(cs.ncand[v], A.nslots);
+    const unsigned nc = cs.ncand[v];
     const uint64_t fb = A.fbase[v];
     const unsigned cap = A.fcap[v];
-    if (tid < nb) {
-      const int c = cs.cslot[(size_t)v * A.nslots + tid];
-      S.hcid[tid] = c;
-#pragma unroll
-      for (int kk = 0; kk < D; ++kk) S.hc[kk][tid] = cs.cg[(size_t)kk * A.cand_cap + c];
-      S.hedge[tid] = cs.cedge[c];
-      S.hpar[tid] = cs.cparent[c];
-    }
-    if (tid < NW) {
-      S.hkill[tid] = 0;
-      S.hpkill[tid] = 0;
+    unsigned ka, kb;
+    part_shape(k, nc, ka, kb);
+    const unsigned a = r % ka, b = r / ka;
+    const unsigned lo = (unsigned)((uint64_t)F * b / kb), hi = (unsigned)((uint64_t)F * (b + 1) / kb);
+    const unsigned ns = min(nc, A.nslots), nl = nc - ns;
+    if (tid < 32) {  // this share's lists (the node's heads stay until the last part resets them)
+      const unsigned j = a + tid * ka;
+      S.hlist[tid] = (j < (1u << A.lsub) && j < nl) ? cs.node_head[((size_t)v << A.lsub) + j] : kNil;
+      if (tid == 0) S.mq_next = 0;
     }
     __syncthreads();
-    const unsigned nwords = (nb + 31) / 32;
-    {  // (a) in-set resolution, candidate tid (every block alike)
-      bool alive = tid < nb;
-      if (alive) {
-        uint32_t ct[D];
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) ct[kk] = S.hc[kk][tid];
-        const uint32_t et = S.hedge[tid];
-        for (unsigned j = 0; j < nb && alive; ++j) {
-          if (j == tid) continue;
-          uint32_t cj[D];
-#pragma unroll
-          for (int kk = 0; kk < D; ++kk) cj[kk] = S.hc[kk][j];
-          const uint32_t ej = S.hedge[j];
-          if (dominates<D>(cj, ct) || (equal<D>(cj, ct) && (ej < et || (ej == et && j < tid)))) alive = false;
-        }
-      }
-      const unsigned am = __ballot_sync(0xffffffffu, alive);
-      if (lane == 0 && w < NW) S.halive[w] = am;
-    }
-    __syncthreads();
-    // (b) this block's range of the frontier, read only
-    const unsigned lo = (unsigned)((uint64_t)F * r / k), hi = (unsigned)((uint64_t)F * (r + 1) / k);
+    const unsigned nrows = ns > a ? (ns - a + ka - 1) / ka : 0u;
     unsigned long long fcmp = 0;
-    for (unsigned r0 = lo + w * 32u * U; r0 < hi; r0 += nw * 32u * U) {
-      uint32_t m[U][D];
-      uint32_t mid[U];
+    bool any_pruned = false;
+    for (;;) {
+      const unsigned nb = gather_group(cs, v, nrows, a, ka, false);
+      if (nb == 0) break;
+      const unsigned nwords = (nb + 31) / 32;
+      load_group(cs, nb);
+      __syncthreads();
+      group_inset(nb);
+      __syncthreads();
+      // (b) the frontier range, read only, until no candidate of the group lives
+      for (unsigned r0 = lo + w * 32u * U; r0 < hi; r0 += nw * 32u * U) {
+        bool any = false;
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const unsigned i = r0 + u * 32 + lane;
-        const bool vm = i < hi;
+        for (unsigned q = 0; q < NW; ++q) any |= q < nwords && (S.halive[q] & ~S.hkill[q]) != 0u;
+        if (!any) break;
+        uint32_t m[U][D];
+        uint32_t mid[U];
 #pragma unroll
-        for (int kk = 0; kk < D; ++kk) m[u][kk] = vm ? A.fpool[fb + (size_t)kk * cap + i] : kInf;
-        mid[u] = vm ? A.fpool[fb + (size_t)D * cap + i] : 0u;
-      }
-      unsigned kill[NW];
+        for (int u = 0; u < U; ++u) {
+          const unsigned i = r0 + u * 32 + lane;
+          const bool vm = i < hi;
 #pragma unroll
-      for (unsigned q = 0; q < NW; ++q) kill[q] = 0;
+          for (int kk = 0; kk < D; ++kk) m[u][kk] = vm ? A.fpool[fb + (size_t)kk * cap + i] : kInf;
+          mid[u] = vm ? A.fpool[fb + (size_t)D * cap + i] : 0u;
+        }
+        unsigned kill[NW];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const unsigned i0 = r0 + u * 32;
-        const bool vm = i0 + lane < hi;
-        bool pruned = false;
-        if (i0 < hi) {
+        for (unsigned q = 0; q < NW; ++q) kill[q] = 0;
 #pragma unroll
-          for (unsigned q = 0; q < NW; ++q) {
-            if (q >= nwords) break;
-            unsigned am = S.halive[q] & ~S.hkill[q] & ~kill[q];
-            fcmp += (unsigned long long)__popc(am) * min(32u, hi - i0);
-            while (am) {
-              const unsigned j = __ffs(am) - 1;
-              am &= am - 1;
-              uint32_t cj[D];
+        for (int u = 0; u < U; ++u) {
+          const unsigned i0 = r0 + u * 32;
+          const bool vm = i0 + lane < hi;
+          bool pruned = false;
+          if (i0 < hi) {
 #pragma unroll
-              for (int kk = 0; kk < D; ++kk) cj[kk] = S.hc[kk][q * 32 + j];
-              const bool le_mc = vm && weakly_le<D>(m[u], cj);
-              const bool le_cm = vm && weakly_le<D>(cj, m[u]);
-              if (__ballot_sync(0xffffffffu, le_mc)) kill[q] |= 1u << j;
-              pruned |= le_cm && !le_mc;
+            for (unsigned q = 0; q < NW; ++q) {
+              if (q >= nwords) break;
+              unsigned am = S.halive[q] & ~S.hkill[q] & ~kill[q];
+              fcmp += (unsigned long long)__popc(am) * min(32u, hi - i0);
+              while (am) {
+                const unsigned j = __ffs(am) - 1;
+                am &= am - 1;
+                uint32_t cj[D];
+#pragma unroll
+                for (int kk = 0; kk < D; ++kk) cj[kk] = S.hc[kk][q * 32 + j];
+                const bool le_mc = vm && weakly_le<D>(m[u], cj);
+                const bool le_cm = vm && weakly_le<D>(cj, m[u]);
+                if (__ballot_sync(0xffffffffu, le_mc)) kill[q] |= 1u << j;
+                pruned |= le_cm && !le_mc;
+              }
             }
           }
+          if (vm && pruned) {
+            A.ldead[mid[u]] = cyc;
+            st[S_PRUNED]++;
+            any_pruned = true;
+          }
         }
-        if (vm && pruned) {
-          A.ldead[mid[u]] = cyc;
-          st[S_PRUNED]++;
-        }
-      }
-      if (lane == 0) {
+        if (lane == 0) {
 #pragma unroll
-        for (unsigned q = 0; q < NW; ++q)
-          if (kill[q]) atomicOr(&S.hkill[q], kill[q]);
+          for (unsigned q = 0; q < NW; ++q)
+            if (kill[q]) atomicOr(&S.hkill[q], kill[q]);
+        }
       }
+      __syncthreads();
+      if (tid < nb) {
+        const unsigned q = tid >> 5, bit = 1u << (tid & 31);
+        if ((S.hkill[q] & bit) || !(S.halive[q] & bit)) cs.cflag[S.hcid[tid]] = 1u;
+      }
+      __syncthreads();  // the next group reuses the shared arrays
     }
     if (lane == 0) st[S_FCMP] += fcmp;
-    __syncthreads();
-    // (c) F against P for the candidate words q = r, r + k, ...: the block's
-    // warps split each word's P log tail and index tiles
-    const unsigned nq = r < nwords ? (nwords - r + k - 1) / k : 0u;
-    if (nq) {
-      const unsigned q = r + (w % nq) * k, nsl = nw / nq, sl = w / nq;
-      const unsigned word = S.halive[q] & ~S.hkill[q];
-      if (word && sl < nsl) {
-        const PIdx& pd = S.pd;
-        const unsigned jj = q * 32 + lane;
-        uint32_t F2[D];
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) F2[kk] = S.hc[kk][jj] + hk(kk, v);
-        bool alive = (word >> lane) & 1u;
-        const unsigned t0 = pd.count ? pd.mark : 0u, t1 = psnap;
-        const unsigned tper = ((t1 - min(t0, t1) + nsl - 1) / nsl + 31) / 32 * 32;
-        const unsigned plo = min(t1, t0 + sl * tper), phi = min(t1, plo + tper);
-        const unsigned nt = pd.count ? pd.ntiles : 0u;
-        const unsigned gper = ((nt + nsl - 1) / nsl + 31) / 32 * 32;
-        const unsigned glo = min(nt, sl * gper), ghi = min(nt, glo + gper);
-        unsigned long long pcmp = 0;
-        p_filter(alive, F2, plo, phi, pd.count, glo, ghi, nt, pd.cur, pcmp);
-        st[S_PCMP] += pcmp;
-        const unsigned pk = __ballot_sync(0xffffffffu, !alive) & word;
-        if (lane == 0 && pk) atomicOr(&S.hpkill[q], pk);
-      }
-    }
-    __syncthreads();
-    if (tid < nb) {
-      const unsigned q = tid >> 5, bit = 1u << (tid & 31);
-      if (((S.hkill[q] | S.hpkill[q]) & bit) || (r == 0 && !(S.halive[q] & bit))) cs.cflag[S.hcid[tid]] = 1u;
-    }
+    // the part counter's low 16 bits count finished parts; kPartPruned is
+    // added by a part that pruned a frontier entry
+    const unsigned pr = __syncthreads_or(any_pruned) ? kPartPruned : 0u;
     __threadfence();
-    __syncthreads();
-    if (tid == 0) S.m_ok = atomicAdd(&cs.hcnt[v], 1u) == k - 1 ? 1u : 0u;
-    __syncthreads();
-    if (!S.m_ok) return;
-    // the last block of the node
-    __threadfence();
-    if (tid < 32) {
-      const Cursor q = open_cursor(cs, v);
-      if (tid == 0) {
-        cs.hcnt[v] = 0;
-        S.mq_ncand = q.ncand;
-        S.mq_next = min(q.ncand, A.nslots);  // the slots are done here; the list remains
-        S.m_next = q.list;
-      }
+    if (tid == 0) {
+      const unsigned c = atomicAdd(&cs.hcnt[v], 1u + pr) + 1u + pr;
+      S.m_ok = (c & (kPartPruned - 1u)) == k ? (c >= kPartPruned ? 2u : 1u) : 0u;
     }
-    const bool surv = tid < nb && __ldcg(cs.cflag + S.hcid[tid]) == 0u;
-    const unsigned out = compact_pruned(fb, cap, F);
-    heavy_insert(v, K1, surv, out, fb, cap);
     __syncthreads();
-    heavy_groups(v, K1);
+    const unsigned ok = S.m_ok;
+    if (!ok) return;
+    // the last part of the node: the survivors of every share
+    __threadfence();
+    open_block_cursor(cs, v, false);
+    if (tid == 0) cs.hcnt[v] = 0;
+    unsigned out = F;
+    if (ok == 2u) {  // some part pruned an entry: compact
+      out = compact_pruned(fb, cap, F);
+      if (tid == 0) A.fcount[v] = out;
+    }
+    __syncthreads();
+    heavy_groups(v, K1, true, out);
   }
 
   // ---------------- P index rebuild (three steps, then published) ----------------
@@ -1725,7 +1823,7 @@ struct Search {
     bpn = next_bins(K0);
     for (unsigned x = threadIdx.x; x < kNB; x += blockDim.x) S.hist[x] = 0;
     if (threadIdx.x == 0) {
-      S.tmax[0] = S.tmax[1] = S.tmax[2] = 0;
+      for (int j = 0; j < 5; ++j) S.tmax[j] = 0;
       const volatile PIdx* src = &C->pidx[cur];
       S.pd.cur = src->cur;
       S.pd.count = src->count;
@@ -1744,6 +1842,8 @@ struct Search {
         st[S_MAXH] += K2.tmax[0];
         st[S_MAXL] += K2.tmax[1];
         st[S_MAXX] += K2.tmax[2];
+        st[S_MAXNC] += K2.tmax[3];
+        st[S_MAXF] += K2.tmax[4];
         clear_cycle(K2);
         // values step i+1 starts from; the writers of this step raise them
         atomicMax(&K1.plen.v, psnap);
@@ -1763,24 +1863,34 @@ struct Search {
       st[S_TSEL] += t - *tlap;
       *tlap = t;
     }
-    // block merges first (the longest single tasks): item t is range
-    // t / nh of heavy node t % nh; a node split into k ranges uses ranges
-    // 0..k-1, the other items are skipped
-    for (const unsigned nhi = nh * kSplitMax; nhi;) {
+    // block merges first (the longest single tasks): the parts of split
+    // merges (recorded in xpart while the candidates arrived), then one item
+    // per heavy node, skipped when the node's merge is split
+    const unsigned np = ld_volatile(&K0.part_count.v);
+    for (const unsigned nhi = np + nh; nhi;) {
       if (threadIdx.x == 0) S.claim = atomicAdd(&K0.heavy_next.v, 1u);
       __syncthreads();
       const unsigned t = S.claim;
       __syncthreads();
       if (t >= nhi) break;
-      const unsigned h = t % nh, r = t / nh;
+      const unsigned x = t < np ? A.cs[cur].xpart[t] : (t - np) << 4;
+      const unsigned h = x >> 4, r = x & 15u;
       const unsigned k = A.cs[cur].hsplit[h];
-      if (r >= k) continue;
+      if (t >= np && k > 1u) continue;
       const uint32_t v = A.cs[cur].touched[2u * A.cand_cap - 1u - h];
+      if (threadIdx.x == 0 && r == 0) {  // read before the merge clears them
+        S.tmax[3] = max(S.tmax[3], A.cs[cur].ncand[v]);
+        S.tmax[4] = max(S.tmax[4], A.fcount[v]);
+      }
       const unsigned long long t0 = globaltimer();
-      if (k == 1)
+      if constexpr (Team::kSplitMerges) {
+        if (k > 1u)
+          merge_part(v, r, k, K1);
+        else
+          merge_heavy(v, K1);
+      } else {
         merge_heavy(v, K1);
-      else
-        merge_range(v, r, k, K1);
+      }
       if (threadIdx.x == 0) {
         S.tmax[0] = max(S.tmax[0], (unsigned)min(globaltimer() - t0, 0xFFFFFFFFull));
         st[S_NHEAVY] += r == 0;
@@ -1820,7 +1930,7 @@ struct Search {
     }
     index_strided_work(T);
     __syncthreads();
-    if (threadIdx.x < 3) atomicMax(&K0.tmax[threadIdx.x], S.tmax[threadIdx.x]);
+    if (threadIdx.x < 5) atomicMax(&K0.tmax[threadIdx.x], S.tmax[threadIdx.x]);
     for (unsigned x = threadIdx.x; x < kNB; x += blockDim.x)
       if (S.hist[x]) atomicAdd(&A.hist[r1 * kNB + x], S.hist[x]);
     if (T.leader() && tlap) {
@@ -2056,6 +2166,7 @@ __global__ void __launch_bounds__(kGridThreads, 1) search_grid_kernel(GraphDev G
 // least one block), so large and small queries advance side by side.
 // ---------------------------------------------------------------------------
 struct SubTeam {
+  static constexpr bool kSplitMerges = false;  // a query's arena has kparts = 1
   unsigned j, nb;
   __device__ __forceinline__ unsigned tid() const { return j * blockDim.x + threadIdx.x; }
   __device__ __forceinline__ unsigned nthreads() const { return nb * blockDim.x; }

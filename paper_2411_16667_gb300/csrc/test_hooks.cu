@@ -54,9 +54,9 @@ __global__ void __launch_bounds__(kGridThreads, 1) merge_hook_kernel(GraphDev G,
     for (int i = 0; i < kNB; ++i) S.hist[i] = 0;
   }
   __syncthreads();
-  if (block >= 2) {  // the split merge, its ranges one after the other (the last one finishes)
+  if (block >= 2) {  // a merge split into `block` parts, one after the other (the last one finishes)
     for (unsigned r = 0; r < block; ++r) {
-      X.merge_range(0u, r, block, C->cyc[1]);
+      X.merge_part(0u, r, block, C->cyc[1]);
       __syncthreads();
     }
   } else if (block) {
@@ -68,12 +68,14 @@ __global__ void __launch_bounds__(kGridThreads, 1) merge_hook_kernel(GraphDev G,
 
 template <int D>
 int merge_hook(uint32_t nfront, const uint32_t* front, uint32_t ncand, const uint32_t* cand, const uint32_t* arc,
-               uint32_t block, uint32_t slots, uint32_t* out_cost, uint32_t* out_origin, uint32_t* out_count) {
+               uint32_t block, uint32_t slots, uint32_t lsub, uint32_t* out_cost, uint32_t* out_origin,
+               uint32_t* out_count) {
   const uint32_t n = 1;  // node 0, and node 1 standing for P
   const uint32_t label_cap = nfront + ncand + 64, cand_cap = ncand + 64, open_cap = ncand + 64;
   const uint32_t fcap0 = (nfront + 31) / 32 * 32 + 32;
   const size_t fpool_words = (size_t)(D + 1) * (fcap0 + 4 * (nfront + ncand) + 256);
-  size_t bytes = 64 * 256 + sizeof(QCtl) + (size_t)D * 4 * (n + 1) + 8 * 4 * (n + 1) + 2 * (4 * (n + 1) * (3 + slots)) +
+  size_t bytes = 64 * 256 + sizeof(QCtl) + (size_t)D * 4 * (n + 1) + 8 * 4 * (n + 1) +
+                 2 * (4 * (n + 1) * (3 + slots + (1u << lsub))) +
                  2 * (size_t)cand_cap * (32 + 4 * D) + 2 * 4 * (n + 1) + (size_t)label_cap * (4 * D + 20) + fpool_words * 4 +
                  2 * (size_t)open_cap * 12 + 3 * kNB * 4 + kPSMax * 4 + 64 * 4 * D * 6;
   DevBuf mem;
@@ -90,7 +92,7 @@ int merge_hook(uint32_t nfront, const uint32_t* front, uint32_t ncand, const uin
   for (int b = 0; b < 2; ++b) {
     CandSet& cs = A.cs[b];
     cs.ncand = take<uint32_t>(p, n + 1);
-    cs.node_head = take<int32_t>(p, n + 1);
+    cs.node_head = take<int32_t>(p, (size_t)(n + 1) << lsub);
     cs.hflag = take<uint32_t>(p, n + 1);
     cs.hcnt = take<uint32_t>(p, n + 1);
     cs.hsplit = take<uint32_t>(p, cand_cap);
@@ -126,10 +128,11 @@ int merge_hook(uint32_t nfront, const uint32_t* front, uint32_t ncand, const uin
   A.plog_cap = 64;
   A.fpool_words = fpool_words;
   A.nslots = slots;
+  A.lsub = lsub;
   if ((size_t)(p - base) > bytes) return hook_fail(OPMOS_ERR_CAPACITY, "test hook: layout exceeds its buffer");
   e = cudaMemset(mem.p, 0, bytes);
   // host images of what a step finds: frontier of node 0 (labels 0..nfront-1)
-  // and the candidates of node 0 in set 0 (slots, then the list)
+  // and the candidates of node 0 in set 0 (slots, then the lists)
   std::vector<uint32_t> fimg((size_t)(D + 1) * fcap0, 0), lg((size_t)label_cap * D, 0), lnode(label_cap, 0),
       lpar(label_cap, kInf), ledge(label_cap, kInf), ldead(label_cap, kAlive);
   for (uint32_t i = 0; i < nfront; ++i) {
@@ -140,16 +143,18 @@ int merge_hook(uint32_t nfront, const uint32_t* front, uint32_t ncand, const uin
     fimg[(size_t)D * fcap0 + i] = i;
   }
   std::vector<uint32_t> cnode(cand_cap, 0), cpar(cand_cap, 0), cedge(cand_cap, 0), cg((size_t)cand_cap * D, 0);
-  std::vector<int32_t> cnext(cand_cap, kNil), cslot((size_t)(n + 1) * slots, kNil), head(n + 1, kNil);
+  std::vector<int32_t> cnext(cand_cap, kNil), cslot((size_t)(n + 1) * slots, kNil),
+      head((size_t)(n + 1) << lsub, kNil);
   for (uint32_t j = 0; j < ncand; ++j) {
     cpar[j] = j;
     cedge[j] = arc[j];
     for (int k = 0; k < D; ++k) cg[(size_t)k * cand_cap + j] = cand[(size_t)j * D + k];
     if (j < slots) {
       cslot[j] = (int32_t)j;
-    } else {  // the list, newest first, as the expansion's exchanges leave it
-      cnext[j] = head[0];
-      head[0] = (int32_t)j;
+    } else {  // list (j - slots) mod 2^lsub, newest first, as the expansion's exchanges leave it
+      const uint32_t l = (j - slots) & ((1u << lsub) - 1u);
+      cnext[j] = head[l];
+      head[l] = (int32_t)j;
     }
   }
   const uint32_t ncand_v[2] = {ncand, 0};
@@ -186,7 +191,7 @@ int merge_hook(uint32_t nfront, const uint32_t* front, uint32_t ncand, const uin
   up(cs.cedge, cedge.data(), cedge.size() * 4);
   up(cs.cnext, cnext.data(), cnext.size() * 4);
   up(cs.cg, cg.data(), cg.size() * 4);
-  std::vector<int32_t> nil1(n + 1, kNil);
+  std::vector<int32_t> nil1((size_t)(n + 1) << lsub, kNil);
   up(A.cs[1].node_head, nil1.data(), nil1.size() * 4);
   if (e != cudaSuccess) return hook_fail(OPMOS_ERR_CUDA, "test hook upload: %s", cudaGetErrorString(e));
   GraphDev G{};
@@ -261,26 +266,35 @@ __global__ void __launch_bounds__(kGridThreads, 1) window_hook_kernel(GraphDev G
 extern "C" {
 
 int opmos_test_merge(uint32_t d, uint32_t nfront, const uint32_t* front, uint32_t ncand, const uint32_t* cand,
-                     const uint32_t* cand_arc, uint32_t block, uint32_t slots, uint32_t* out_cost,
-                     uint32_t* out_origin, uint32_t* out_count) {
+                     const uint32_t* cand_arc, uint32_t block, uint32_t slots, uint32_t lists,
+                     uint32_t* out_cost, uint32_t* out_origin, uint32_t* out_count) {
   try {
     if (!out_cost || !out_origin || !out_count || (nfront && !front) || (ncand && (!cand || !cand_arc)))
       return hook_fail(OPMOS_ERR_INVALID_ARG, "NULL argument");
     if (slots == 0 || slots > 4096) return hook_fail(OPMOS_ERR_INVALID_ARG, "slots must be in [1, 4096]");
-    if (block > kSplitMax) return hook_fail(OPMOS_ERR_INVALID_ARG, "block must be 0..%u", kSplitMax);
-    if (block >= 2 && slots > kHC) return hook_fail(OPMOS_ERR_INVALID_ARG, "a split merge holds at most %u slots", kHC);
+    if (block > kPartsMax) return hook_fail(OPMOS_ERR_INVALID_ARG, "block must be 0..%u", kPartsMax);
     if (nfront > (1u << 20) || ncand > (1u << 20)) return hook_fail(OPMOS_ERR_INVALID_ARG, "inputs too large");
+    unsigned lsub = 0;
+    while ((1u << lsub) < lists && lsub < 5) ++lsub;
+    if (lists == 0 || lists != (1u << lsub))
+      return hook_fail(OPMOS_ERR_INVALID_ARG, "lists must be 1, 2, 4, 8, 16 or 32");
     switch (d) {
-      case 1: return merge_hook<1>(nfront, front, ncand, cand, cand_arc, block, slots, out_cost, out_origin, out_count);
-      case 2: return merge_hook<2>(nfront, front, ncand, cand, cand_arc, block, slots, out_cost, out_origin, out_count);
-      case 3: return merge_hook<3>(nfront, front, ncand, cand, cand_arc, block, slots, out_cost, out_origin, out_count);
-      case 4: return merge_hook<4>(nfront, front, ncand, cand, cand_arc, block, slots, out_cost, out_origin, out_count);
-      case 5: return merge_hook<5>(nfront, front, ncand, cand, cand_arc, block, slots, out_cost, out_origin, out_count);
-      case 8: return merge_hook<8>(nfront, front, ncand, cand, cand_arc, block, slots, out_cost, out_origin, out_count);
+      case 1:
+        return merge_hook<1>(nfront, front, ncand, cand, cand_arc, block, slots, lsub, out_cost, out_origin, out_count);
+      case 2:
+        return merge_hook<2>(nfront, front, ncand, cand, cand_arc, block, slots, lsub, out_cost, out_origin, out_count);
+      case 3:
+        return merge_hook<3>(nfront, front, ncand, cand, cand_arc, block, slots, lsub, out_cost, out_origin, out_count);
+      case 4:
+        return merge_hook<4>(nfront, front, ncand, cand, cand_arc, block, slots, lsub, out_cost, out_origin, out_count);
+      case 5:
+        return merge_hook<5>(nfront, front, ncand, cand, cand_arc, block, slots, lsub, out_cost, out_origin, out_count);
+      case 8:
+        return merge_hook<8>(nfront, front, ncand, cand, cand_arc, block, slots, lsub, out_cost, out_origin, out_count);
       case 12:
-        return merge_hook<12>(nfront, front, ncand, cand, cand_arc, block, slots, out_cost, out_origin, out_count);
+        return merge_hook<12>(nfront, front, ncand, cand, cand_arc, block, slots, lsub, out_cost, out_origin, out_count);
       case 16:
-        return merge_hook<16>(nfront, front, ncand, cand, cand_arc, block, slots, out_cost, out_origin, out_count);
+        return merge_hook<16>(nfront, front, ncand, cand, cand_arc, block, slots, lsub, out_cost, out_origin, out_count);
       default:
         return hook_fail(OPMOS_ERR_INVALID_ARG, "d = %u has no merge test hook", d);
     }

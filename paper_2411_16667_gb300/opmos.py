@@ -9,6 +9,7 @@ from __future__ import annotations
 import ctypes
 import dataclasses
 import os
+from collections.abc import Sequence
 
 import numpy as np
 
@@ -27,7 +28,7 @@ EXPORTS = ("opmos_default_options", "opmos_device_count", "opmos_graph_create", 
            "opmos_solve_batch", "opmos_result_count", "opmos_result_d", "opmos_result_costs",
            "opmos_result_path", "opmos_result_stats", "opmos_result_free", "opmos_server_create",
            "opmos_server_submit", "opmos_server_poll", "opmos_server_destroy", "opmos_last_error",
-           "opmos_heuristic_noalloc")
+           "opmos_heuristic_noalloc", "opmos_result_paths")
 
 
 class OpmosError(RuntimeError):
@@ -50,7 +51,8 @@ class Stats(ctypes.Structure):
         ("phase_ns", ctypes.c_uint64 * 4), ("goal_inserted", ctypes.c_uint64),
         ("open_scanned", ctypes.c_uint64), ("open_rewritten", ctypes.c_uint64),
         ("list_candidates", ctypes.c_uint64), ("longest_task_ns", ctypes.c_uint64 * 3),
-        ("heavy_merges", ctypes.c_uint64)]
+        ("heavy_merges", ctypes.c_uint64), ("heavy_max_candidates", ctypes.c_uint64),
+        ("heavy_max_frontier", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         arrays = ("phase_ns", "longest_task_ns")
@@ -88,6 +90,7 @@ def lib(path: str | None = None):
         L.opmos_result_d.restype = u32
         L.opmos_result_costs.argtypes = [vp, vp]
         L.opmos_result_path.argtypes = [vp, u32, vp, vp, u32, ctypes.POINTER(u32)]
+        L.opmos_result_paths.argtypes = [vp, vp, vp, vp]
         L.opmos_result_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.opmos_result_free.argtypes = [vp]
         L.opmos_result_free.restype = None
@@ -98,7 +101,7 @@ def lib(path: str | None = None):
         L.opmos_server_destroy.restype = None
         L.opmos_last_error.restype = ctypes.c_char_p
         L.opmos_heuristic_noalloc.argtypes = [vp, u32, u32, vp, vp]
-        L.opmos_test_merge.argtypes = [u32, u32, vp, u32, vp, vp, u32, u32, vp, vp, ctypes.POINTER(u32)]
+        L.opmos_test_merge.argtypes = [u32, u32, vp, u32, vp, vp, u32, u32, u32, vp, vp, ctypes.POINTER(u32)]
         L.opmos_test_window.argtypes = [u32, vp, vp, vp, u32, vp, vp, ctypes.POINTER(u32)]
         _lib = L
     return _lib
@@ -193,8 +196,31 @@ def opmos_heuristic_noalloc(graph: opmos_graph, goal: int, d_used: int, h_out_de
 @dataclasses.dataclass
 class Result:
     costs: np.ndarray  # uint32 [count, d], lexicographic
-    paths: list | None  # [(nodes uint32, edges uint64)] or None
+    paths: "Paths | None"  # paths[i] = (nodes uint32, edges uint64), or None
     stats: dict
+
+
+class Paths(Sequence):
+    """The paths of a result, one per cost vector, over three flat arrays
+    (``opmos_result_paths``): ``paths[i]`` is (nodes, arc ids), views of
+    ``nodes[offsets[i]:offsets[i+1]]`` and ``edges[offsets[i]-i:offsets[i+1]-i-1]``."""
+
+    def __init__(self, offsets: np.ndarray, nodes: np.ndarray, edges: np.ndarray):
+        self.offsets, self.nodes, self.edges = offsets, nodes, edges
+
+    def __len__(self) -> int:
+        return int(self.offsets.shape[0]) - 1
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self[j] for j in range(*i.indices(len(self)))]
+        n = len(self)
+        if i < 0:
+            i += n
+        if not 0 <= i < n:
+            raise IndexError(i)
+        a, b = int(self.offsets[i]), int(self.offsets[i + 1])
+        return self.nodes[a:b], self.edges[a - i:b - i - 1]
 
 
 def _take(res) -> Result:
@@ -206,18 +232,14 @@ def _take(res) -> Result:
             _check(L.opmos_result_costs(res, _ptr(costs)), "opmos_result_costs")
         st = Stats()
         _check(L.opmos_result_stats(res, ctypes.byref(st)), "opmos_result_stats")
-        paths = []
-        ln = ctypes.c_uint32()
-        for i in range(cnt):
-            rc = L.opmos_result_path(res, i, None, None, 0, ctypes.byref(ln))
-            if rc == ERR_INVALID_ARG:
-                paths = None
-                break
-            nodes = np.empty(ln.value, np.uint32)
-            edges = np.empty(max(ln.value - 1, 0), np.uint64)
-            _check(L.opmos_result_path(res, i, _ptr(nodes), _ptr(edges) if edges.size else None, ln.value,
-                                       ctypes.byref(ln)), "opmos_result_path")
-            paths.append((nodes, edges))
+        offs = np.zeros(cnt + 1, np.uint32)
+        paths = None
+        if L.opmos_result_paths(res, _ptr(offs), None, None) == OK:
+            total = int(offs[cnt])
+            nodes = np.empty(max(total, 1), np.uint32)
+            edges = np.empty(max(total - cnt, 1), np.uint64)
+            _check(L.opmos_result_paths(res, _ptr(offs), _ptr(nodes), _ptr(edges)), "opmos_result_paths")
+            paths = Paths(offs, nodes[:total], edges[:total - cnt])
         return Result(costs, paths, st.as_dict())
     finally:
         L.opmos_result_free(res)
@@ -303,12 +325,13 @@ class opmos_server:
 # ---------------------------------------------------------------------------
 # test hooks (include/opmos_test.h): single device routines on given inputs
 # ---------------------------------------------------------------------------
-def opmos_test_merge(front, cand, cand_arc, block, slots: int = 32):
+def opmos_test_merge(front, cand, cand_arc, block, slots: int = 32, lists: int = 1):
     """Device merge of one node (frontier rows ``front``, candidate rows
-    ``cand`` with arc ids ``cand_arc``) by one warp (block 0), one block (1)
-    or a block merge split over ``block`` = 2..4 frontier ranges; returns
-    (costs, origins) of the frontier after the merge (origin < len(front):
-    that entry; else len(front) + candidate index)."""
+    ``cand`` with arc ids ``cand_arc``; the first ``slots`` in the node's
+    slots, the rest in ``lists`` overflow lists) by one warp (block 0), one
+    block (1) or a block merge split into ``block`` = 2..16 parts;
+    returns (costs, origins) of the frontier after the merge (origin <
+    len(front): that entry; else len(front) + candidate index)."""
     front = np.ascontiguousarray(front, np.uint32)
     cand = np.ascontiguousarray(cand, np.uint32)
     arc = np.ascontiguousarray(cand_arc, np.uint32)
@@ -317,8 +340,8 @@ def opmos_test_merge(front, cand, cand_arc, block, slots: int = 32):
     out = np.zeros((nf + nc + 1, d), np.uint32)
     org = np.zeros(nf + nc + 1, np.uint32)
     cnt = ctypes.c_uint32()
-    _check(lib().opmos_test_merge(d, nf, _ptr(front), nc, _ptr(cand), _ptr(arc), int(block), slots, _ptr(out),
-                                  _ptr(org), ctypes.byref(cnt)), "opmos_test_merge")
+    _check(lib().opmos_test_merge(d, nf, _ptr(front), nc, _ptr(cand), _ptr(arc), int(block), slots, lists,
+                                  _ptr(out), _ptr(org), ctypes.byref(cnt)), "opmos_test_merge")
     return out[:cnt.value], org[:cnt.value]
 
 

@@ -37,6 +37,14 @@ int main(void) {
   uint64_t edges[8];
   if (opmos_result_path(r, 0, nodes, edges, 8, &len) != OPMOS_OK || len != 3) return 24;
   if (nodes[0] != 0 || nodes[1] != 1 || nodes[2] != 3 || edges[0] != 0 || edges[1] != 3) return 25;
+  /* every path at once: 0 -> 1 -> 3 (arcs 0, 3) and 0 -> 2 -> 3 (arcs 1, 4) */
+  uint32_t offs[3] = {0}, all_nodes[6];
+  uint64_t all_edges[4];
+  if (opmos_result_paths(r, offs, NULL, NULL) != OPMOS_OK || offs[0] != 0 || offs[1] != 3 || offs[2] != 6) return 26;
+  if (opmos_result_paths(r, offs, all_nodes, all_edges) != OPMOS_OK) return 27;
+  if (all_nodes[3] != 0 || all_nodes[4] != 2 || all_nodes[5] != 3 || all_edges[0] != 0 || all_edges[1] != 3 ||
+      all_edges[2] != 1 || all_edges[3] != 4)
+    return 28;
   opmos_result_free(r);
   opmos_graph_destroy(g);
   printf("front (4,5) (5,4)\n");

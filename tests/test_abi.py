@@ -46,7 +46,7 @@ def test_options_struct_matches_defaults():
     assert (o.window, o.lanes_per_label, o.tile, o.delta) == (1024, 8, 32, 1)
     assert o.mem_budget_bytes == 8 << 30
     assert ctypes.sizeof(opmos.Options) == 48
-    assert ctypes.sizeof(opmos.Stats) == 25 * 8
+    assert ctypes.sizeof(opmos.Stats) == 27 * 8
 
 
 @pytest.mark.skipif(opmos.opmos_device_count() > 0, reason="only meaningful without a GPU")

@@ -31,7 +31,7 @@ def test_traffic_digest_covers_the_kernel_sources_and_launch_options():
     assert len(a) == 16 and a == bench.kernel_source_digest((1024, 8, 32, 1))
     assert a != bench.kernel_source_digest((512, 8, 32, 1))
     assert all(os.path.exists(os.path.join(ROOT, f)) for f in bench.KERNEL_SOURCES)
-    assert isinstance(bench.TRAFFIC["bytes_per_launch"], int) and bench.TRAFFIC["bytes_per_launch"] > 0
+    assert all(len(k) == 16 and isinstance(v, int) and v > 0 for k, v in bench.TRAFFIC.items())
 
 
 def test_kernel_digest_ignores_comments_only():

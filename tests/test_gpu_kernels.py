@@ -65,18 +65,23 @@ def _reference(front, cand, arc):
     return sorted(keep)
 
 
-CASES = [  # (d, frontier size, candidates, slots)
-    (1, 1, 5, 32), (2, 31, 20, 32), (2, 32, 33, 32), (3, 33, 31, 32), (3, 100, 70, 32), (3, 511, 40, 128),
-    (3, 512, 33, 32), (4, 513, 64, 32), (5, 200, 100, 128), (8, 60, 45, 32), (3, 3000, 50, 32),
-    (12, 40, 40, 32), (16, 25, 35, 32), (2, 0, 40, 32)]
+CASES = [  # (d, frontier size, candidates, slots, overflow lists)
+    (1, 1, 5, 32, 1), (2, 31, 20, 32, 32), (2, 32, 33, 32, 1), (3, 33, 31, 32, 8), (3, 100, 70, 32, 32),
+    (3, 511, 40, 128, 32), (3, 512, 33, 32, 2), (4, 513, 64, 32, 8), (5, 200, 100, 128, 8), (8, 60, 45, 32, 32),
+    (3, 3000, 50, 32, 1), (12, 40, 40, 32, 4), (16, 25, 35, 32, 32), (2, 0, 40, 32, 16),
+    # many candidates beyond the slots: several rounds over the lists, groups of a block merge
+    (3, 600, 700, 32, 32), (2, 50, 300, 16, 32), (5, 300, 1000, 64, 8), (4, 150, 530, 128, 16), (3, 80, 200, 8, 1),
+    # many slot candidates: split merges whose parts split the candidates (and groups of 256 within a part)
+    (3, 900, 1000, 1024, 32), (2, 2000, 600, 1024, 32), (4, 300, 700, 512, 8), (8, 200, 400, 1024, 32),
+    (3, 5000, 90, 1024, 32)]
 
 
-@pytest.mark.parametrize("d,nf,nc,slots", CASES)
-@pytest.mark.parametrize("block", [0, 1, 3])
-def test_node_merge_matches_host_reference(op, d, nf, nc, slots, block):
-    """block: 0 one warp, 1 one block, 3 a block merge split over three
-    ranges of the frontier (candidates beyond the slots go through the
-    list after the split part)."""
+@pytest.mark.parametrize("d,nf,nc,slots,lists", CASES)
+@pytest.mark.parametrize("block", [0, 1, 3, 8])
+def test_node_merge_matches_host_reference(op, d, nf, nc, slots, lists, block):
+    """block: 0 one warp, 1 one block, 3 or 8 a block merge split into that
+    many parts (ranges of the slot candidates times ranges of the frontier;
+    candidates beyond the slots go through the lists after the parts)."""
     rng = np.random.default_rng(1000 * d + nf + nc + int(block))
     hi = 40 if nf < 400 else 400
     front = _antichain(rng, nf, d, hi) if nf else np.zeros((0, d), np.uint32)
@@ -90,7 +95,7 @@ def test_node_merge_matches_host_reference(op, d, nf, nc, slots, block):
     if nf < 40:
         cand[-4] = 0      # the zero vector dominates everything non-zero
     arc = rng.permutation(10 * nc)[:nc].astype(np.uint32)
-    costs, origin = op.opmos_test_merge(front, cand, arc, block, slots)
+    costs, origin = op.opmos_test_merge(front, cand, arc, block, slots, lists)
     got = sorted((tuple(int(v) for v in c), int(o)) for c, o in zip(costs, origin))
     assert got == _reference(front, cand, arc)
 
