@@ -623,7 +623,7 @@ def run_order(args, opmos, torch, stream):
     g, q = synth.config2()
     G = opmos.opmos_graph.from_synth(g)
     rows = []
-    for w in (256, 1024, 4096):
+    for w in (256, 1024, 4096, 16384, 65536, 262144):
         for name, flags in (("ordered", 0), ("fifo", opmos.FLAG_FIFO)):
             opt = opmos.opmos_default_options(stream=stream.cuda_stream, window=w, flags=flags)
             r = opmos.opmos_solve(G, *q[0], options=opt)

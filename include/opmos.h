@@ -139,6 +139,8 @@ typedef struct opmos_stats {
                               or many candidates in the step) */
   uint64_t heavy_max_candidates; /* summed over steps: the most candidates, and the largest */
   uint64_t heavy_max_frontier;   /* frontier, of a node merged by whole blocks in the step */
+  uint64_t task_ns[3];     /* summed durations of all block merges (one block each), one-warp
+                              merges and extraction items (one warp each) */
 } opmos_stats;
 
 /* Fill *opt with the defaults (all fields explicit). */

@@ -370,6 +370,9 @@ void fill_stats(opmos_stats* s, const QResult& R, uint32_t D) {
   s->heavy_merges = R.stats[S_NHEAVY];
   s->heavy_max_candidates = R.stats[S_MAXNC];
   s->heavy_max_frontier = R.stats[S_MAXF];
+  s->task_ns[0] = R.stats[S_SUMH];
+  s->task_ns[1] = R.stats[S_SUML];
+  s->task_ns[2] = R.stats[S_SUMX];
   // algorithmic bytes: per extracted label 8d+12 (g, node, rowptr pair, F key),
   // per candidate 4+8d (col, cost, h), per compared frontier/P entry 4d, per
   // inserted label 4d+24 (label record, frontier slot, OPEN entry), per prune 4.

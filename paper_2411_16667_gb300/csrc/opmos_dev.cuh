@@ -79,6 +79,9 @@ enum StatIdx {
   S_NHEAVY,   // heavy merges
   S_MAXNC,    // sum over steps of the most candidates a block-merged node of the step had
   S_MAXF,     // ... of the largest frontier a block-merged node of the step had
+  S_SUMH,     // summed durations of block merges (one block each), ns
+  S_SUML,     // ... of one-warp merges (one warp each)
+  S_SUMX,     // ... of extraction work items (one warp each)
   kNStat
 };
 

@@ -1892,8 +1892,10 @@ struct Search {
         merge_heavy(v, K1);
       }
       if (threadIdx.x == 0) {
-        S.tmax[0] = max(S.tmax[0], (unsigned)min(globaltimer() - t0, 0xFFFFFFFFull));
+        const unsigned long long dt = globaltimer() - t0;
+        S.tmax[0] = max(S.tmax[0], (unsigned)min(dt, 0xFFFFFFFFull));
         st[S_NHEAVY] += r == 0;
+        st[S_SUMH] += dt;
       }
     }
     // warp items: index-rank items, light merges, extraction chunks
@@ -1918,14 +1920,22 @@ struct Search {
         } else {
           merge_node(v, K1);
         }
-        if (lane == 0) atomicMax(&S.tmax[1], (unsigned)min(globaltimer() - t0, 0xFFFFFFFFull));
+        if (lane == 0) {
+          const unsigned long long dt = globaltimer() - t0;
+          atomicMax(&S.tmax[1], (unsigned)min(dt, 0xFFFFFFFFull));
+          st[S_SUML] += dt;
+        }
       } else {
         const unsigned c = t - nrank - nt;
         if (fifo)
           extract_fifo(head + c * kChunk, head + min(fwin, (c + 1) * kChunk), K1);
         else
           extract_chunk(c, n_in, bp, K1);
-        if (lane == 0) atomicMax(&S.tmax[2], (unsigned)min(globaltimer() - t0, 0xFFFFFFFFull));
+        if (lane == 0) {
+          const unsigned long long dt = globaltimer() - t0;
+          atomicMax(&S.tmax[2], (unsigned)min(dt, 0xFFFFFFFFull));
+          st[S_SUMX] += dt;
+        }
       }
     }
     index_strided_work(T);

@@ -52,10 +52,10 @@ class Stats(ctypes.Structure):
         ("open_scanned", ctypes.c_uint64), ("open_rewritten", ctypes.c_uint64),
         ("list_candidates", ctypes.c_uint64), ("longest_task_ns", ctypes.c_uint64 * 3),
         ("heavy_merges", ctypes.c_uint64), ("heavy_max_candidates", ctypes.c_uint64),
-        ("heavy_max_frontier", ctypes.c_uint64)]
+        ("heavy_max_frontier", ctypes.c_uint64), ("task_ns", ctypes.c_uint64 * 3)]
 
     def as_dict(self) -> dict:
-        arrays = ("phase_ns", "longest_task_ns")
+        arrays = ("phase_ns", "longest_task_ns", "task_ns")
         d = {f: int(getattr(self, f)) for f, _ in self._fields_ if f not in arrays}
         for f in arrays:
             d[f] = [int(x) for x in getattr(self, f)]

@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_2411_16667_gb300 as pkg
@@ -46,7 +47,7 @@ def test_options_struct_matches_defaults():
     assert (o.window, o.lanes_per_label, o.tile, o.delta) == (1024, 8, 32, 1)
     assert o.mem_budget_bytes == 8 << 30
     assert ctypes.sizeof(opmos.Options) == 48
-    assert ctypes.sizeof(opmos.Stats) == 27 * 8
+    assert ctypes.sizeof(opmos.Stats) == 30 * 8
 
 
 @pytest.mark.skipif(opmos.opmos_device_count() > 0, reason="only meaningful without a GPU")
@@ -93,3 +94,20 @@ def test_plain_c_client_solves_on_the_device(tmp_path):
     if opmos.opmos_device_count() == 0:
         pytest.fail("no CUDA device visible to the library")
     assert "front (4,5) (5,4)" in _run_c_client(tmp_path)
+
+
+def test_paths_are_views_of_the_flat_arrays():
+    """Result.paths over opmos_result_paths' layout: path i's nodes are
+    nodes[offsets[i]:offsets[i+1]] and its arcs edges[offsets[i]-i:offsets[i+1]-i-1]."""
+    offs = np.array([0, 3, 4, 7], np.uint32)
+    nodes = np.array([10, 11, 12, 20, 30, 31, 32], np.uint32)
+    edges = np.array([100, 101, 300, 301], np.uint64)
+    p = opmos.Paths(offs, nodes, edges)
+    assert len(p) == 3
+    assert p[0][0].tolist() == [10, 11, 12] and p[0][1].tolist() == [100, 101]
+    assert p[1][0].tolist() == [20] and p[1][1].size == 0
+    assert p[-1][0].tolist() == [30, 31, 32] and p[-1][1].tolist() == [300, 301]
+    assert [n.tolist() for n, _ in p[1:]] == [[20], [30, 31, 32]]
+    assert [len(n) for n, _ in p] == [3, 1, 3]
+    with pytest.raises(IndexError):
+        p[3]
