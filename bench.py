@@ -482,7 +482,13 @@ def run_batch(args, opmos, torch, stream):
     calib = q[::32]
     ch = autotune.autotune(G, calib, mode="batch", windows=(128, 256, 1024), lanes=(8, 16), tiles=(32, 64),
                            stream_ptr=stream.cuda_stream)
-    opt = ch.options(stream=stream.cuda_stream, flags=opmos.FLAG_GRAPH)
+    # the window of the queries that outgrow the shared launch (alone_labels):
+    # tuned on the calibration queries farthest apart, solved alone
+    dist = grid_distance(g, calib)
+    far = [calib[i] for i in sorted(range(len(calib)), key=lambda i: -dist[i])[:4]]
+    alone_window = autotune.autotune(G, far, mode="single", windows=(1024, 4096, 16384, 65536), lanes=(8,),
+                                     tiles=(32,), stream_ptr=stream.cuda_stream).window
+    opt = ch.options(stream=stream.cuda_stream, flags=opmos.FLAG_GRAPH, alone_window=alone_window)
     if args.window:
         opt.window = args.window
     for _ in range(args.warmup):
@@ -501,9 +507,10 @@ def run_batch(args, opmos, torch, stream):
     sec = max_over_ranks(statistics.median(times))
     if rank != 0:
         return
-    # one query per launch on an evenly spaced sample of the same queries
+    # one query per launch on an evenly spaced sample of the same queries,
+    # with the window the batch gives the queries it solves alone
     sample = q[::16]
-    single = opmos.opmos_default_options(stream=stream.cuda_stream)
+    single = opmos.opmos_default_options(stream=stream.cuda_stream, window=alone_window)
     t0 = time.perf_counter()
     for s_, t_ in sample:
         opmos.opmos_solve(G, s_, t_, options=single)
@@ -519,6 +526,9 @@ def run_batch(args, opmos, torch, stream):
                       "queries_ok": ok, "labels_extracted": sum(r.stats["extracted"] for r in rs),
                       "labels_per_s": sum(r.stats["extracted"] for r in rs) / sec,
                       "batch_kernel_ms": statistics.median(r.stats["search_ns"] for r in rs) / 1e6,
+                      "queries_alone": sum(1 for r in rs if r.stats["search_ns"] != statistics.median_low(
+                          x.stats["search_ns"] for x in rs)),
+                      "alone_labels": opt.alone_labels or 1_000_000, "alone_window": alone_window,
                       "heuristic_ms": rs[0].stats["heuristic_ns"] / 1e6,
                       "one_query_per_launch_qps": single_qps,
                       "one_query_per_launch_sample": f"{len(sample)} of the 1,024 queries (every 16th)",

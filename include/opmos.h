@@ -91,6 +91,14 @@ typedef struct opmos_options {
   uint32_t d_used;           /* use only the first d_used objectives (Table 1 order rule,
                                 Sec. 6.1). Default: all. */
   uint32_t flags;            /* OPMOS_FLAG_* */
+  uint64_t alone_labels;     /* batch: a query that creates more labels than this in its slot of
+                                the shared launch leaves it and is solved alone afterwards, on
+                                the whole device with the same options but the window
+                                alone_window (so with the front and paths opmos_solve gives
+                                with that window). Default 1,000,000; UINT64_MAX: never. */
+  uint32_t alone_window;     /* batch: the window of the queries solved alone. Default: the
+                                window opmos_solve would take from these options. */
+  uint32_t reserved;         /* 0 */
   void* stream;              /* cudaStream_t the work is issued on; NULL = default stream. */
 } opmos_options;
 

@@ -184,6 +184,8 @@ opmos_options resolve(const opmos_options* in, bool batch) {
   if (in->label_budget) o.label_budget = in->label_budget;
   if (in->mem_budget_bytes) o.mem_budget_bytes = in->mem_budget_bytes;
   if (in->d_used) o.d_used = in->d_used;
+  if (in->alone_labels) o.alone_labels = in->alone_labels;
+  if (in->alone_window) o.alone_window = in->alone_window;
   o.flags = in->flags;
   o.stream = in->stream;
   return o;
@@ -196,6 +198,7 @@ int check_options(const opmos_options& o, const opmos_graph* g, uint32_t* d_used
     return fail(OPMOS_ERR_INVALID_ARG, "lanes_per_label must be 4, 8, 16 or 32");
   if (o.tile % 32 || o.tile == 0) return fail(OPMOS_ERR_INVALID_ARG, "tile must be a positive multiple of 32");
   if (o.window == 0 || o.window > (1u << 22)) return fail(OPMOS_ERR_INVALID_ARG, "window out of range");
+  if (o.alone_window > (1u << 22)) return fail(OPMOS_ERR_INVALID_ARG, "alone_window out of range");
   *d_used = du;
   return OPMOS_OK;
 }
@@ -458,6 +461,7 @@ unsigned long long time_limit_ns() {
   return kTimeLimitNs;
 }
 constexpr unsigned kBatchSlots = 192;  // concurrent queries of a batch
+constexpr uint64_t kAloneLabels = 1000000;  // default alone_labels
 // P-index rebuild thresholds (log growth beyond 32 + count >> grow): the
 // whole grid ranks a single query's index fast; a multi-query slot has only
 // its share of the blocks, so it rebuilds less often.
@@ -586,7 +590,10 @@ int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const st
   P.lanes = o.lanes_per_label;
   P.delta = o.delta;
   P.tile = o.tile;
-  P.label_budget = (uint32_t)std::min<uint64_t>(o.label_budget ? o.label_budget : ~0ull, pl.label_cap);
+  // the slot's label budget: the query's own, or the point past which it is
+  // solved alone instead (a lower one), within what the slot holds
+  const uint64_t own = o.label_budget ? o.label_budget : ~0ull;
+  P.label_budget = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(own, o.alone_labels), pl.label_cap);
   P.flags = o.flags;
   P.qd = D;
   P.ps_grow = kMultiIndexGrow;
@@ -753,8 +760,8 @@ int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const st
   for (uint32_t i = 0; i < nq; ++i) {
     const uint32_t q = qlist[order[i]];
     const unsigned st = hres[i].status;
-    if (st == OPMOS_ERR_CAPACITY) {
-      overflow->push_back(q);  // outgrew its slot: next round
+    if (st == OPMOS_ERR_CAPACITY || (st == OPMOS_ERR_BUDGET && P.label_budget < own)) {
+      overflow->push_back(q);  // outgrew its slot or the shared launch: solved alone
       continue;
     }
     if (st != 0) {
@@ -789,6 +796,7 @@ void opmos_default_options(opmos_options* o) {
   o->mem_budget_bytes = 8ull << 30;
   o->d_used = 0;
   o->flags = 0;
+  o->alone_labels = kAloneLabels;
   o->stream = nullptr;
 }
 
@@ -982,25 +990,23 @@ int opmos_solve_batch(const opmos_graph* g, uint32_t nq, const uint32_t* starts,
     } free_h{hall};
     uint64_t hns = 0;
     if (int rc = compute_heuristic(g, D, ugoals.data(), (uint32_t)ugoals.size(), hall, s, &hns)) return rc;
-    // Rounds of the multi-query kernel: all queries, then those that outgrew
-    // their slot with 8x fewer, 8x larger slots; single-query mode last.
+    // One launch of the multi-query kernel for all queries; those that
+    // outgrow their slot, or pass alone_labels, are solved alone afterwards.
     std::vector<uint32_t> todo(nq);
     for (uint32_t q = 0; q < nq; ++q) todo[q] = q;
-    unsigned slots = std::min<unsigned>(nq, std::min<unsigned>(kMaxSlots, kBatchSlots));
-    for (int round = 0; round < 3 && !todo.empty(); ++round) {
-      slots = std::max(1u, std::min<unsigned>(slots, (unsigned)todo.size()));
+    {
+      const unsigned slots = std::max(1u, std::min<unsigned>(nq, std::min<unsigned>(kMaxSlots, kBatchSlots)));
       std::vector<uint32_t> overflow;
       if (int rc = run_multi(g, D, o, todo, starts, goals, hall, gidx, slots, o.mem_budget_bytes / slots, hns, t0, out,
                              status, &overflow))
         return rc;
       todo.swap(overflow);
-      slots = slots / 8;
-      if (slots < 2) break;
     }
     if (!todo.empty()) {
       opmos_options so = resolve(opt, false);
       so.flags = o.flags;
       so.stream = o.stream;
+      if (o.alone_window) so.window = o.alone_window;
       if (opt && opt->mem_budget_bytes) so.mem_budget_bytes = std::max<uint64_t>(opt->mem_budget_bytes, 1ull << 30);
       for (uint32_t q : todo) {
         opmos_result* r = nullptr;

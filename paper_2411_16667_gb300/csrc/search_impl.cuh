@@ -138,7 +138,7 @@ struct Shared {
   uint32_t hedge[kHC], hpar[kHC];
   unsigned halive[kHC / 32], hkill[kHC / 32], hpkill[kHC / 32];
   int hlist[32];       // cursors of the block-merged node's lists
-  unsigned mq_ncand, mq_next, m_nb, m_ok, m_lb, m_cap;
+  unsigned mq_ncand, mq_next, m_nb, m_ok, m_lb, m_cap, m_plen;
   unsigned long long m_fb;
   unsigned tmax[5];    // this block's longest heavy merge, light merge, extraction item (ns);
                        // most candidates and largest frontier of its heavy merges
@@ -417,8 +417,8 @@ struct Search {
     // whole blocks; its light item then only clears hflag. Only light items
     // touch hflag during the merge, so a block merge never races a warp.
     if (pos == 0) cs.touched[agg_inc(&K1.touched_count.v)] = v2;
-    if (v2 == G.n) return;
-    // (the work of a one-warp merge grows with frontier x candidates)
+    // (the work of a one-warp merge grows with frontier x candidates; at the
+    // goal node n, with candidates x P)
     const bool list = pos == kHeavyCands ||
                       ((pos == 0 || pos == kHeavyCands / 2 - 1) &&
                        A.fcount[v2] >= (pos ? kHeavyFrontier * 3 / 8 : kHeavyFrontier));
@@ -1247,9 +1247,11 @@ struct Search {
   }
 
   // F against P for the live candidates of group word q, this warp taking
-  // slice sl of nsl of the P log tail and of the index tiles; the ones P
-  // dominates are flagged in S.hpkill.
-  __device__ void group_ptest(uint32_t v, unsigned q, unsigned nsl, unsigned sl) {
+  // slice sl of nsl of the P log entries [t0, t1) and of the first nt index
+  // tiles; the ones P dominates are flagged in S.hpkill. At the goal node n,
+  // F = g (h(n) = 0).
+  __device__ void group_ptest(uint32_t v, unsigned q, unsigned nsl, unsigned sl, unsigned t0, unsigned t1,
+                              unsigned nt) {
     const unsigned lane = lane_id();
     const unsigned word = S.halive[q] & ~S.hkill[q];
     if (!word || sl >= nsl) return;
@@ -1257,12 +1259,10 @@ struct Search {
     const unsigned jj = q * 32 + lane;
     uint32_t F[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) F[k] = S.hc[k][jj] + hk(k, v);
+    for (int k = 0; k < D; ++k) F[k] = S.hc[k][jj] + (v == G.n ? 0u : hk(k, v));
     bool alive = (word >> lane) & 1u;
-    const unsigned t0 = pd.count ? pd.mark : 0u, t1 = psnap;
     const unsigned tper = ((t1 - min(t0, t1) + nsl - 1) / nsl + 31) / 32 * 32;
     const unsigned lo = min(t1, t0 + sl * tper), hi = min(t1, lo + tper);
-    const unsigned nt = pd.count ? pd.ntiles : 0u;
     const unsigned gper = ((nt + nsl - 1) / nsl + 31) / 32 * 32;
     const unsigned glo = min(nt, sl * gper), ghi = min(nt, glo + gper);
     unsigned long long pcmp = 0;
@@ -1276,8 +1276,12 @@ struct Search {
   // (S.mq_ncand candidates, slots from S.mq_next, then the lists at
   // S.hlist). filtered: the survivors of a split merge's parts (the ones
   // without cflag), already checked against the frontier's first `old`
-  // entries, so only the entries the loop itself inserts are scanned.
-  __device__ void heavy_groups(uint32_t v, CycleCtl& K1, bool filtered, unsigned old = 0) {
+  // entries, so only the entries the loop itself inserts are scanned. At the
+  // goal node n there is no frontier scan: alpha(n) is P, and candidates meet
+  // P through the P index and log, up to the entries this merge appended
+  // (from entry pfrom on only, when filtered: the parts tested the rest).
+  __device__ void heavy_groups(uint32_t v, CycleCtl& K1, bool filtered, unsigned old = 0, unsigned pfrom = 0) {
+    const bool goal = v == G.n;
     constexpr int U = kUH;
     constexpr unsigned NW = kHC / 32;  // candidate words
     const CandSet& cs = A.cs[cyc & 1u];
@@ -1296,10 +1300,10 @@ struct Search {
       const uint64_t fb = A.fbase[v];
       const unsigned cap = A.fcap[v];
       const unsigned fc = A.fcount[v];
-      unsigned out = old;
+      unsigned out = goal ? fc : old;
       unsigned long long fcmp = 0;
       const unsigned R = nw * 32u * U;
-      for (unsigned r0 = old; r0 < fc; r0 += R) {
+      for (unsigned r0 = out; r0 < fc; r0 += R) {
         const unsigned base = r0 + w * 32u * U;
         uint32_t m[U][D];
         uint32_t mid[U];
@@ -1397,7 +1401,14 @@ struct Search {
       if (lane == 0) st[S_FCMP] += fcmp;
       // (c) F against P: warp w takes candidate word w % nwords and one of the
       // nw / nwords slices of the P log tail and of the index tiles
-      group_ptest(v, w % nwords, nw / nwords, w / nwords);
+      {
+        const unsigned pl = goal ? ld_volatile(&C->plog_len.v) : psnap;
+        if (goal && filtered)
+          group_ptest(v, w % nwords, nw / nwords, w / nwords, pfrom, pl, 0u);
+        else
+          group_ptest(v, w % nwords, nw / nwords, w / nwords, S.pd.count ? S.pd.mark : 0u, pl,
+                      S.pd.count ? S.pd.ntiles : 0u);
+      }
       __syncthreads();
       // (d) survivors become labels, join alpha(v) and the next OPEN
       const bool surv = tid < nb && (((S.halive[w % NW] & ~S.hkill[w % NW] & ~S.hpkill[w % NW]) >> lane) & 1u);
@@ -1408,11 +1419,12 @@ struct Search {
 
   // Survivors of a block merge (thread tid holds candidate tid in shared
   // memory; surv tells whether it survived) become labels, join alpha(v) --
-  // out live entries at fb, cap, grown when full -- and the next OPEN.
-  // Returns alpha(v)'s new size (the block must pass a barrier before the
-  // shared candidate arrays are reused).
+  // out live entries at fb, cap, grown when full -- and the next OPEN, or at
+  // the goal node n the P log. Returns alpha(v)'s new size (the block must
+  // pass a barrier before the shared candidate arrays are reused).
   __device__ unsigned heavy_insert(uint32_t v, CycleCtl& K1, bool surv, unsigned out, uint64_t fb, unsigned cap) {
     const unsigned tid = threadIdx.x, lane = lane_id(), w = tid >> 5, nw = blockDim.x >> 5;
+    const bool goal = v == G.n;
     const unsigned smask = __ballot_sync(0xffffffffu, surv);
     if (lane == 0) S.warp[w] = __popc(smask);
     __syncthreads();
@@ -1432,9 +1444,12 @@ struct Search {
         S.m_lb = lb;
         if (lb + ntot > A.label_cap || lb + ntot > P.label_budget) {
           set_error(C, (lb + ntot > A.label_cap) ? OPMOS_ERR_CAPACITY : OPMOS_ERR_BUDGET);
+        } else if (goal && ld_volatile(&C->plog_len.v) + ntot > A.plog_cap) {
+          set_error(C, OPMOS_ERR_CAPACITY);
         } else {
           atomicMax(&K1.lbase.v, lb + ntot);
           S.m_ok = 1;
+          S.m_plen = goal ? ld_volatile(&C->plog_len.v) : 0u;  // this block is the log's only writer
           if (out + ntot > cap) {  // grow: a new block of twice the size
             const unsigned tile = P.tile;
             unsigned ncap = max(2u * (out + ntot), tile);
@@ -1468,7 +1483,7 @@ struct Search {
         for (int k = 0; k < D; ++k) c[k] = S.hc[k][tid];
 #pragma unroll
         for (int k = 0; k < D; ++k) A.lg[(size_t)k * A.label_cap + id] = c[k];
-        A.lnode[id] = v;
+        A.lnode[id] = goal ? P.goal : v;
         A.lparent[id] = S.hpar[tid];
         A.ledge[id] = S.hedge[tid];
         A.lpver[id] = psnap;
@@ -1476,7 +1491,20 @@ struct Search {
 #pragma unroll
         for (int k = 0; k < D; ++k) A.fpool[nfb + (size_t)k * ncap + out + rank] = c[k];
         A.fpool[nfb + (size_t)D * ncap + out + rank] = id;
-        push_open(id, c, v, K1);
+        if (goal) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) A.plog[(size_t)k * A.plog_cap + S.m_plen + rank] = c[k];
+        } else {
+          push_open(id, c, v, K1);
+        }
+      }
+      if (goal) {
+        __syncthreads();  // the log entries are written before they are published
+        if (tid == 0) {
+          __threadfence();
+          *reinterpret_cast<volatile unsigned*>(&C->plog_len.v) = S.m_plen + ntot;
+          atomicMax(&K1.plen.v, S.m_plen + ntot);
+        }
       }
       if (tid == 0) {
         A.fbase[v] = nfb;
@@ -1569,7 +1597,10 @@ struct Search {
   // the frontier is an antichain). The last part to finish (a counter per
   // node; nobody waits) compacts the frontier if a part pruned, then merges
   // the surviving candidates as one block merge does -- against each other,
-  // the entries it inserts and P -- so P tests only the survivors.
+  // the entries it inserts and P -- so P tests only the survivors. At the goal
+  // node n, whose alpha is P, the parts split the candidates only and test
+  // them against P; the last part tests the survivors against the log
+  // entries it appends itself.
   __device__ void merge_part(uint32_t v, unsigned r, unsigned k, CycleCtl& K1) {
     constexpr int U = kUH;
     constexpr unsigned NW = kHC / 32;
@@ -1579,10 +1610,11 @@ struct Search {
     const unsigned nc = cs.ncand[v];
     const uint64_t fb = A.fbase[v];
     const unsigned cap = A.fcap[v];
-    unsigned ka, kb;
-    part_shape(k, nc, ka, kb);
+    const bool goal = v == G.n;  // no frontier ranges: the parts test their shares against P
+    unsigned ka = k, kb = 1;
+    if (!goal) part_shape(k, nc, ka, kb);
     const unsigned a = r % ka, b = r / ka;
-    const unsigned lo = (unsigned)((uint64_t)F * b / kb), hi = (unsigned)((uint64_t)F * (b + 1) / kb);
+    const unsigned lo = (unsigned)((uint64_t)F * b / kb), hi = goal ? 0u : (unsigned)((uint64_t)F * (b + 1) / kb);
     const unsigned ns = min(nc, A.nslots), nl = nc - ns;
     if (tid < 32) {  // this share's lists (the node's heads stay until the last part resets them)
       const unsigned j = a + tid * ka;
@@ -1657,9 +1689,14 @@ struct Search {
         }
       }
       __syncthreads();
+      if (goal) {  // P as the parts see it: no part appends to the log
+        group_ptest(v, w % nwords, nw / nwords, w / nwords, S.pd.count ? S.pd.mark : 0u,
+                    ld_volatile(&C->plog_len.v), S.pd.count ? S.pd.ntiles : 0u);
+        __syncthreads();
+      }
       if (tid < nb) {
         const unsigned q = tid >> 5, bit = 1u << (tid & 31);
-        if ((S.hkill[q] & bit) || !(S.halive[q] & bit)) cs.cflag[S.hcid[tid]] = 1u;
+        if (((S.hkill[q] | S.hpkill[q]) & bit) || !(S.halive[q] & bit)) cs.cflag[S.hcid[tid]] = 1u;
       }
       __syncthreads();  // the next group reuses the shared arrays
     }
@@ -1685,7 +1722,7 @@ struct Search {
       if (tid == 0) A.fcount[v] = out;
     }
     __syncthreads();
-    heavy_groups(v, K1, true, out);
+    heavy_groups(v, K1, true, out, ld_volatile(&C->plog_len.v));
   }
 
   // ---------------- P index rebuild (three steps, then published) ----------------

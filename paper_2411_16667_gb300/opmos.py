@@ -41,6 +41,7 @@ class Options(ctypes.Structure):
     _fields_ = [("window", ctypes.c_uint32), ("lanes_per_label", ctypes.c_uint32), ("tile", ctypes.c_uint32),
                 ("delta", ctypes.c_uint32), ("label_budget", ctypes.c_uint64),
                 ("mem_budget_bytes", ctypes.c_uint64), ("d_used", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("alone_labels", ctypes.c_uint64), ("alone_window", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("stream", ctypes.c_void_p)]
 
 

@@ -46,7 +46,8 @@ def test_options_struct_matches_defaults():
     o = opmos.opmos_default_options()
     assert (o.window, o.lanes_per_label, o.tile, o.delta) == (1024, 8, 32, 1)
     assert o.mem_budget_bytes == 8 << 30
-    assert ctypes.sizeof(opmos.Options) == 48
+    assert ctypes.sizeof(opmos.Options) == 64 and o.alone_window == 0
+    assert o.alone_labels == 1_000_000
     assert ctypes.sizeof(opmos.Stats) == 30 * 8
 
 
