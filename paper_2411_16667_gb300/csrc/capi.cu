@@ -527,6 +527,7 @@ int solve_one(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint
   P.flags = o.flags;
   P.qd = D;
   P.ps_grow = kGridIndexGrow;
+  P.heavy_work = o.window < kSmallWindow ? kHeavyWorkSmallWindow : kHeavyWork;
   P.time_limit_ns = time_limit_ns();
 
   int occ = search_occupancy(D);
@@ -597,6 +598,7 @@ int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const st
   P.flags = o.flags;
   P.qd = D;
   P.ps_grow = kMultiIndexGrow;
+  P.heavy_work = kHeavyWork;
   P.time_limit_ns = time_limit_ns();
   std::vector<MSlot> hslots(slots);
   for (unsigned i = 0; i < slots; ++i) {
@@ -1244,6 +1246,7 @@ int opmos_server_create(const opmos_graph* const* graphs, uint32_t ngraphs, cons
       sl.P.flags = o.flags;
       sl.P.qd = sv->dmax;
       sl.P.ps_grow = kMultiIndexGrow;
+      sl.P.heavy_work = kHeavyWork;
       sl.P.time_limit_ns = time_limit_ns();
       sl.state = SL_FREE;
     }

@@ -37,7 +37,13 @@ constexpr int kSub = 256;    // F[1] cells per F[0] bucket; a bin is 2^s2 consec
 constexpr unsigned kChunk = 32;       // OPEN entries per extraction work item
 constexpr unsigned kRankQ = 1024;     // P entries per rank work item of an index rebuild
 constexpr unsigned kPSMax = 32768;    // largest P indexed by the sorted snapshot
-constexpr unsigned kHeavyFrontier = 512;  // frontiers this large are merged by a whole block
+// candidates x frontier entries from which a node's merge takes a whole block:
+// lower for small windows (a step is short, its longest one-warp merge sets
+// its length), higher for large windows and batches (block merges are most
+// of the work)
+constexpr unsigned kHeavyWorkSmallWindow = 512;
+constexpr unsigned kHeavyWork = 2048;
+constexpr unsigned kSmallWindow = 16384;
 constexpr unsigned kHeavyCands = 32;      // ... and so are nodes reached by more candidates in a step
 // A block merge whose candidates x frontier entries exceed kPartWork is split
 // into parts (up to kPartsMax, each a whole block), each part holding at
@@ -235,6 +241,7 @@ struct QParams {
   uint32_t flags;
   uint32_t qd;            // objectives the query uses (<= the kernel's D; the rest read as 0)
   uint32_t ps_grow;       // the P index is rebuilt once the log outgrows it by 32 + count >> ps_grow
+  uint32_t heavy_work;    // candidates x frontier entries from which a node is merged by a whole block
   unsigned long long time_limit_ns;
 };
 

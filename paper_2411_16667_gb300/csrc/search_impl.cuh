@@ -138,7 +138,7 @@ struct Shared {
   uint32_t hedge[kHC], hpar[kHC];
   unsigned halive[kHC / 32], hkill[kHC / 32], hpkill[kHC / 32];
   int hlist[32];       // cursors of the block-merged node's lists
-  unsigned mq_ncand, mq_next, m_nb, m_ok, m_lb, m_cap, m_plen;
+  unsigned mq_ncand, mq_next, m_nb, m_ok, m_lb, m_cap, m_plen, m_more;
   unsigned long long m_fb;
   unsigned tmax[5];    // this block's longest heavy merge, light merge, extraction item (ns);
                        // most candidates and largest frontier of its heavy merges
@@ -417,14 +417,19 @@ struct Search {
     // whole blocks; its light item then only clears hflag. Only light items
     // touch hflag during the merge, so a block merge never races a warp.
     if (pos == 0) cs.touched[agg_inc(&K1.touched_count.v)] = v2;
-    // (the work of a one-warp merge grows with frontier x candidates; at the
-    // goal node n, with candidates x P)
+    // A node is merged by a whole block once its candidates x frontier
+    // entries reach P.heavy_work (checked at 1, 4, 8 and 16 candidates: the
+    // work of a one-warp merge grows with that product; at the goal node n,
+    // with candidates x P), and always past kHeavyCands candidates (a warp
+    // would take them in two batches).
+    const unsigned nc = pos + 1u;
     const bool list = pos == kHeavyCands ||
-                      ((pos == 0 || pos == kHeavyCands / 2 - 1) &&
-                       A.fcount[v2] >= (pos ? kHeavyFrontier * 3 / 8 : kHeavyFrontier));
+                      ((nc == 1u || nc == 4u || nc == 8u || nc == 16u) &&
+                       (unsigned long long)nc * A.fcount[v2] >= P.heavy_work);
     // at 64, 128, 256, ... candidates the merge may be split further
     const bool grow = A.kparts > 1u && pos > kHeavyCands && ((pos + 1u) & pos) == 0u;
-    if (list || grow) heavy_list(cs, K1, v2, parts_for(pos + 1u, A.fcount[v2]), list);
+    // (the P test of a goal candidate skips most of P through the index tiles)
+    if (list || grow) heavy_list(cs, K1, v2, parts_for(pos + 1u, A.fcount[v2] >> (v2 == G.n ? 3 : 0)), list);
   }
 
   // Parts a block merge of nc candidates against F frontier entries is split
@@ -1169,11 +1174,16 @@ struct Search {
                                    bool filtered) {
     const unsigned tid = threadIdx.x;
     unsigned s0 = S.mq_next, n0 = 0;
+    if (!filtered) {  // every slot below the count holds a candidate
+      n0 = s0 < nrows ? min(kHC, nrows - s0) : 0u;
+      if (tid < n0) S.hcid[tid] = cs.cslot[(size_t)v * A.nslots + first + (s0 + tid) * stride];
+      s0 += n0;
+    }
     while (s0 < nrows && n0 < kHC) {  // (uniform: s0 and n0 are the same in every thread)
       const unsigned take = min(kHC - n0, nrows - s0);
       int c = kNil;
       if (tid < take) c = cs.cslot[(size_t)v * A.nslots + first + (s0 + tid) * stride];
-      const bool keep = c != kNil && (!filtered || __ldcg(cs.cflag + c) == 0u);
+      const bool keep = c != kNil && __ldcg(cs.cflag + c) == 0u;
       unsigned cnt;
       const unsigned pos = block_exclusive_scan(keep ? 1u : 0u, S.warp, cnt);  // (every thread has read mq_next)
       if (keep) S.hcid[n0 + pos] = c;
@@ -1196,9 +1206,11 @@ struct Search {
         n = min(kHC, n + __popc(bal));
       }
       S.hlist[tid] = cur;
+      const bool more = s0 < nrows || __any_sync(0xffffffffu, cur != kNil);
       if (tid == 0) {
         S.mq_next = s0;
         S.m_nb = n;
+        S.m_more = more;
       }
     }
     __syncthreads();
@@ -1413,7 +1425,9 @@ struct Search {
       // (d) survivors become labels, join alpha(v) and the next OPEN
       const bool surv = tid < nb && (((S.halive[w % NW] & ~S.hkill[w % NW] & ~S.hpkill[w % NW]) >> lane) & 1u);
       heavy_insert(v, K1, surv, out, fb, cap);
+      const bool more = S.m_more;
       __syncthreads();  // the next group reuses the shared candidate arrays
+      if (!more) break;
     }
   }
 
@@ -1698,7 +1712,9 @@ struct Search {
         const unsigned q = tid >> 5, bit = 1u << (tid & 31);
         if (((S.hkill[q] | S.hpkill[q]) & bit) || !(S.halive[q] & bit)) cs.cflag[S.hcid[tid]] = 1u;
       }
+      const bool more = S.m_more;
       __syncthreads();  // the next group reuses the shared arrays
+      if (!more) break;
     }
     if (lane == 0) st[S_FCMP] += fcmp;
     // the part counter's low 16 bits count finished parts; kPartPruned is
