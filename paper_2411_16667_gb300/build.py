@@ -24,9 +24,9 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "-I", INCLUDE, "-I", CSRC]
 
 
-# objective counts compiled into one object each; the single-query and
-# multi-query kernels of a count take roughly the same time to compile
-D_GROUPS = ((1, 2), (3, 3), (4, 4), (5, 6), (7, 8), (9, 10), (11, 12), (13, 14), (15, 16))
+# one object per objective count: its single-query kernels (both grid
+# shapes) and its multi-query kernel, the objects compiled side by side
+D_GROUPS = tuple((d, d) for d in range(1, 17))
 INST = "search_inst.cu"
 
 

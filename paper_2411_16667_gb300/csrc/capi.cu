@@ -530,14 +530,16 @@ int solve_one(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint
   P.heavy_work = o.window < kSmallWindow ? kHeavyWorkSmallWindow : kHeavyWork;
   P.time_limit_ns = time_limit_ns();
 
-  int occ = search_occupancy(D);
+  // large windows take the wide grid (two blocks per SM)
+  const bool wide = o.window >= kSmallWindow;
+  int occ = search_occupancy(D, wide);
   if (occ <= 0) return fail(OPMOS_ERR_CUDA, "search kernel cannot be resident");
-  const unsigned blocks = (unsigned)di.sms;  // one block of kGridThreads per SM
+  const unsigned blocks = (unsigned)di.sms * (unsigned)std::min(occ, wide ? (int)kGridWideBlocksPerSM : 1);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
-  cudaError_t e = launch_search_grid(D, g->dev, A, C, P, O, R, blocks, s);
+  cudaError_t e = launch_search_grid(D, g->dev, A, C, P, O, R, wide, blocks, s);
   cudaEventRecord(e1, s);
   QResult hr{};
   cudaError_t e2 = e == cudaSuccess ? cudaMemcpyAsync(&hr, R, sizeof(QResult), cudaMemcpyDeviceToHost, s) : e;

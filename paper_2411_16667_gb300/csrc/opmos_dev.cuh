@@ -91,7 +91,13 @@ enum StatIdx {
   kNStat
 };
 
-constexpr unsigned kGridThreads = 512;  // threads per block of the single-query grid
+// Two shapes of the single-query grid: one 512-thread block per SM for short
+// steps (windows below kSmallWindow), two 256-thread blocks per SM for large
+// windows, where block merges are most of a step and the merges of two blocks
+// overlap on one SM (the 128 registers a thread takes allow exactly two).
+constexpr unsigned kGridThreads = 512;
+constexpr unsigned kGridWideThreads = 256;
+constexpr unsigned kGridWideBlocksPerSM = 2;
 
 struct GraphDev {
   uint32_t n, m, d, maxdeg;

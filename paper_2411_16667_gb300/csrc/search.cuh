@@ -54,11 +54,13 @@ struct QResult {
 // Kernel launchers of one objective count D (search_inst.cu instantiates them,
 // one object per group of D values); the kernel of a query with qd < D
 // objectives reads objectives qd..D-1 as 0.
+// wide: the grid of two 256-thread blocks per SM (large windows) instead of
+// one 512-thread block per SM.
 template <int D>
 cudaError_t launch_grid(const GraphDev& G, const QArena& A, QCtl* C, const QParams& P, const OutPool& O,
-                        QResult* R, unsigned blocks, cudaStream_t s);
+                        QResult* R, bool wide, unsigned blocks, cudaStream_t s);
 template <int D>
-int grid_occupancy();
+int grid_occupancy(bool wide);
 template <int D>
 cudaError_t launch_multi_d(MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue, unsigned* hctl,
                            const GraphDev* graphs, QResult* results, unsigned* done_flags, MCtl* M, unsigned blocks,
@@ -68,8 +70,8 @@ int multi_occupancy_d();
 
 // Dispatch on the objective count, 1..OPMOS_MAX_D (search_dispatch.cu).
 cudaError_t launch_search_grid(unsigned d, const GraphDev& G, const QArena& A, QCtl* C, const QParams& P,
-                               const OutPool& O, QResult* R, unsigned blocks, cudaStream_t s);
-int search_occupancy(unsigned d);
+                               const OutPool& O, QResult* R, bool wide, unsigned blocks, cudaStream_t s);
+int search_occupancy(unsigned d, bool wide);
 cudaError_t launch_multi(unsigned d, MSlot* slots, QCtl* ctls, unsigned nslots, const MQuery* queue,
                          unsigned* hctl, const GraphDev* graphs, QResult* results, unsigned* done_flags, MCtl* M,
                          unsigned blocks, cudaStream_t s);

@@ -28,15 +28,15 @@ static_assert(OPMOS_MAX_D == 16, "the dispatch below lists 1..16");
   }
 
 cudaError_t launch_search_grid(unsigned d, const GraphDev& G, const QArena& A, QCtl* C, const QParams& P,
-                               const OutPool& O, QResult* R, unsigned blocks, cudaStream_t s) {
-#define CALL(D) launch_grid<D>(G, A, C, P, O, R, blocks, s)
+                               const OutPool& O, QResult* R, bool wide, unsigned blocks, cudaStream_t s) {
+#define CALL(D) launch_grid<D>(G, A, C, P, O, R, wide, blocks, s)
   OPMOS_DISPATCH_D(d, CALL)
 #undef CALL
   return cudaErrorInvalidValue;
 }
 
-int search_occupancy(unsigned d) {
-#define CALL(D) grid_occupancy<D>()
+int search_occupancy(unsigned d, bool wide) {
+#define CALL(D) grid_occupancy<D>(wide)
   OPMOS_DISPATCH_D(d, CALL)
 #undef CALL
   return 0;

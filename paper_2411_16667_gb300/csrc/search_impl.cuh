@@ -324,7 +324,8 @@ struct Search {
   // but at least the first non-empty bin (the overflow bin is never taken).
   // Every block computes the same b* into S.bstar.
   __device__ void select_window(const unsigned* gh) {
-    constexpr unsigned kPer = kNB / 256;  // bins per thread: blockDim.x is 256 or 512
+    constexpr unsigned kPer = kNB / 256;  // bins per thread: blocks have 256 threads or more
+    static_assert(kGridThreads >= 256 && kGridWideThreads >= 256 && kMultiThreads >= 256, "kPer");
     const unsigned per = (kNB + blockDim.x - 1) / blockDim.x;
     const unsigned b0 = threadIdx.x * per;
     unsigned loc[kPer];
@@ -1164,7 +1165,7 @@ struct Search {
     }
   }
 
-  // The next group (up to kHC) of a block merge's candidates, into S.hcid;
+  // The next group (up to kHC, one per thread) of a block merge's candidates, into S.hcid;
   // returns its size (every thread), 0 once none is left. First the slot
   // rows S.mq_next, S.mq_next + 1, ... below nrows, row j being slot
   // first + j * stride, then the lists whose cursors sit in S.hlist, walked
@@ -1173,14 +1174,15 @@ struct Search {
   __device__ unsigned gather_group(const CandSet& cs, uint32_t v, unsigned nrows, unsigned first, unsigned stride,
                                    bool filtered) {
     const unsigned tid = threadIdx.x;
+    const unsigned hcap = min(kHC, blockDim.x);  // one candidate per thread
     unsigned s0 = S.mq_next, n0 = 0;
     if (!filtered) {  // every slot below the count holds a candidate
-      n0 = s0 < nrows ? min(kHC, nrows - s0) : 0u;
+      n0 = s0 < nrows ? min(hcap, nrows - s0) : 0u;
       if (tid < n0) S.hcid[tid] = cs.cslot[(size_t)v * A.nslots + first + (s0 + tid) * stride];
       s0 += n0;
     }
-    while (s0 < nrows && n0 < kHC) {  // (uniform: s0 and n0 are the same in every thread)
-      const unsigned take = min(kHC - n0, nrows - s0);
+    while (s0 < nrows && n0 < hcap) {  // (uniform: s0 and n0 are the same in every thread)
+      const unsigned take = min(hcap - n0, nrows - s0);
       int c = kNil;
       if (tid < take) c = cs.cslot[(size_t)v * A.nslots + first + (s0 + tid) * stride];
       const bool keep = c != kNil && __ldcg(cs.cflag + c) == 0u;
@@ -1196,14 +1198,14 @@ struct Search {
       unsigned n = n0;
       for (;;) {
         const bool live = cur != kNil;
-        if (!__any_sync(0xffffffffu, live) || n >= kHC) break;
+        if (!__any_sync(0xffffffffu, live) || n >= hcap) break;
         const bool kp = live && (!filtered || __ldcg(cs.cflag + cur) == 0u);
         const unsigned bal = __ballot_sync(0xffffffffu, kp);
         const unsigned rk = __popc(bal & lanemask_lt());
-        const bool put = kp && n + rk < kHC;
+        const bool put = kp && n + rk < hcap;
         if (put) S.hcid[n + rk] = cur;
         if (put || (live && !kp)) cur = cs.cnext[cur];
-        n = min(kHC, n + __popc(bal));
+        n = min(hcap, n + __popc(bal));
       }
       S.hlist[tid] = cur;
       const bool more = s0 < nrows || __any_sync(0xffffffffu, cur != kNil);
@@ -1229,6 +1231,7 @@ struct Search {
       S.hpar[tid] = cs.cparent[c];
     }
     if (tid < kHC / 32) {
+      S.halive[tid] = 0;
       S.hkill[tid] = 0;
       S.hpkill[tid] = 0;
     }
@@ -2209,9 +2212,9 @@ __device__ void run_grid(const GraphDev& G, const QArena& A, QCtl* C, const QPar
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(kGridThreads, 1) search_grid_kernel(GraphDev G, QArena A, QCtl* C, QParams P,
-                                                                      OutPool O, QResult* R) {
+template <int D, unsigned NT, unsigned NB>
+__global__ void __launch_bounds__(NT, NB) search_grid_kernel(GraphDev G, QArena A, QCtl* C, QParams P, OutPool O,
+                                                             QResult* R) {
   run_grid<D>(G, A, C, P, O, R);
 }
 
@@ -2517,16 +2520,25 @@ __global__ void __launch_bounds__(kMultiThreads, 2)
 // ---------------------------------------------------------------------------
 template <int D>
 cudaError_t launch_grid(const GraphDev& G, const QArena& A, QCtl* C, const QParams& P, const OutPool& O,
-                        QResult* R, unsigned blocks, cudaStream_t s) {
+                        QResult* R, bool wide, unsigned blocks, cudaStream_t s) {
   void* args[] = {(void*)&G, (void*)&A, (void*)&C, (void*)&P, (void*)&O, (void*)&R};
-  return cudaLaunchCooperativeKernel((void*)detail::search_grid_kernel<D>, dim3(blocks), dim3(kGridThreads), args,
-                                     0, s);
+  if (wide)
+    return cudaLaunchCooperativeKernel(
+        (void*)detail::search_grid_kernel<D, kGridWideThreads, kGridWideBlocksPerSM>, dim3(blocks),
+        dim3(kGridWideThreads), args, 0, s);
+  return cudaLaunchCooperativeKernel((void*)detail::search_grid_kernel<D, kGridThreads, 1>, dim3(blocks),
+                                     dim3(kGridThreads), args, 0, s);
 }
 
 template <int D>
-int grid_occupancy() {
+int grid_occupancy(bool wide) {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, detail::search_grid_kernel<D>, kGridThreads, 0);
+  if (wide)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &nb, detail::search_grid_kernel<D, kGridWideThreads, kGridWideBlocksPerSM>, kGridWideThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, detail::search_grid_kernel<D, kGridThreads, 1>,
+                                                  kGridThreads, 0);
   return nb;
 }
 

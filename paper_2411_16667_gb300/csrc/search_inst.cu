@@ -11,8 +11,8 @@ namespace opmos {
 
 #define OPMOS_INSTANTIATE(D)                                                                                     \
   template cudaError_t launch_grid<D>(const GraphDev&, const QArena&, QCtl*, const QParams&, const OutPool&,    \
-                                      QResult*, unsigned, cudaStream_t);                                         \
-  template int grid_occupancy<D>();                                                                             \
+                                      QResult*, bool, unsigned, cudaStream_t);                                   \
+  template int grid_occupancy<D>(bool);                                                                         \
   template cudaError_t launch_multi_d<D>(MSlot*, QCtl*, unsigned, const MQuery*, unsigned*, const GraphDev*,     \
                                          QResult*, unsigned*, MCtl*, unsigned, cudaStream_t);                   \
   template int multi_occupancy_d<D>();

@@ -130,14 +130,17 @@ def test_given_heuristic_is_used(op):
     assert res.stats["heuristic_ns"] == 0
 
 
-def test_config2_full_size_against_golden(op):
-    """Full 256x256 3-objective ship grid against the committed oracle front."""
+@pytest.mark.parametrize("window", [1024, 262144])
+def test_config2_full_size_against_golden(op, window):
+    """Full 256x256 3-objective ship grid against the committed oracle front,
+    with the default window (one 512-thread block per SM) and the large
+    window the bench picks (two 256-thread blocks per SM, split merges)."""
     meta, expect = load_front_fixture(os.path.join(GOLDEN, "config2_seed1_q0.front"))
     g, q = synth.config2()
     if g.digest() != meta["digest"]:
         pytest.fail(f"regenerated graph digest {g.digest()} != fixture {meta['digest']}")
     G = op.opmos_graph.from_synth(g)
-    res = op.opmos_solve(G, meta["start"], meta["goal"])
+    res = op.opmos_solve(G, meta["start"], meta["goal"], window=window)
     _same_front(res, expect)
     # the front equals the oracle's bit for bit; every path is re-verified
     check_front_sampled(g, meta["start"], meta["goal"], res.costs, res.paths, nrows=500,
@@ -297,6 +300,11 @@ def test_paths_repeat_exactly(op):
     for r in runs[1:]:
         assert np.array_equal(r.costs, runs[0].costs)
         _same_paths(r, runs[0])
+    # the wide grid (large windows): repeated runs keep their paths too
+    wide = [op.opmos_solve(G, s, t, window=65536) for _ in range(3)]
+    for r in wide[1:]:
+        assert np.array_equal(r.costs, runs[0].costs)
+        _same_paths(r, wide[0])
 
 
 def test_batch_graph_capture_gives_the_same_fronts(op):

@@ -71,13 +71,14 @@ def test_time_routes_against_oracle(op, d):
 
 def test_time_route_d12_large_front(op):
     """A d = 12 route whose front holds about 1,800 vectors (frontiers past
-    the block-merge threshold): single query, default and small windows."""
+    the block-merge threshold): single query, default, small and large
+    windows."""
     g, q = synth.time_route(1, 4, 6, 16, 12)
     s, t = q[0]
     exp = oracle.solve(g, s, t)
     assert len(exp.costs) > 1000
     G = op.opmos_graph.from_synth(g)
-    for w in (1024, 64):
+    for w in (1024, 64, 16384):  # the last one on the wide grid
         res = op.opmos_solve(G, s, t, window=w)
         assert np.array_equal(res.costs, exp.costs)
     check_front(g, s, t, res.costs, res.paths)
