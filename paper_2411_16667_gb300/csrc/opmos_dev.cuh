@@ -48,7 +48,7 @@ constexpr unsigned kHeavyCands = 32;      // ... and so are nodes reached by mor
 // A block merge whose candidates x frontier entries exceed kPartWork is split
 // into parts (up to kPartsMax, each a whole block), each part holding at
 // least kPartCands candidates when the candidates are split.
-constexpr unsigned long long kPartWork = 1ull << 17;
+constexpr unsigned long long kPartWork = 1ull << 18;
 constexpr unsigned kPartsMax = 16;
 constexpr unsigned kPartCands = 64;
 constexpr unsigned kPartPruned = 1u << 16;  // added to a node's part counter by a part that pruned
@@ -92,12 +92,14 @@ enum StatIdx {
 };
 
 // Two shapes of the single-query grid: one 512-thread block per SM for short
-// steps (windows below kSmallWindow), two 256-thread blocks per SM for large
-// windows, where block merges are most of a step and the merges of two blocks
-// overlap on one SM (the 128 registers a thread takes allow exactly two).
+// steps (windows below kSmallWindow), three 256-thread blocks per SM for large
+// windows, where block merges are most of a step and the merges of three
+// blocks overlap on one SM (registers are capped at 85 a thread then, and
+// some spill; two blocks with 128 registers were 9% slower, four with 64
+// no faster).
 constexpr unsigned kGridThreads = 512;
 constexpr unsigned kGridWideThreads = 256;
-constexpr unsigned kGridWideBlocksPerSM = 2;
+constexpr unsigned kGridWideBlocksPerSM = 3;
 
 struct GraphDev {
   uint32_t n, m, d, maxdeg;

@@ -54,8 +54,8 @@ struct QResult {
 // Kernel launchers of one objective count D (search_inst.cu instantiates them,
 // one object per group of D values); the kernel of a query with qd < D
 // objectives reads objectives qd..D-1 as 0.
-// wide: the grid of two 256-thread blocks per SM (large windows) instead of
-// one 512-thread block per SM.
+// wide: the grid of three 256-thread blocks per SM (large windows) instead
+// of one 512-thread block per SM.
 template <int D>
 cudaError_t launch_grid(const GraphDev& G, const QArena& A, QCtl* C, const QParams& P, const OutPool& O,
                         QResult* R, bool wide, unsigned blocks, cudaStream_t s);

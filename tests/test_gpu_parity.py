@@ -134,7 +134,7 @@ def test_given_heuristic_is_used(op):
 def test_config2_full_size_against_golden(op, window):
     """Full 256x256 3-objective ship grid against the committed oracle front,
     with the default window (one 512-thread block per SM) and the large
-    window the bench picks (two 256-thread blocks per SM, split merges)."""
+    window the bench picks (three 256-thread blocks per SM, split merges)."""
     meta, expect = load_front_fixture(os.path.join(GOLDEN, "config2_seed1_q0.front"))
     g, q = synth.config2()
     if g.digest() != meta["digest"]:
