@@ -528,6 +528,7 @@ int solve_one(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint
   P.qd = D;
   P.ps_grow = kGridIndexGrow;
   P.heavy_work = o.window < kSmallWindow ? kHeavyWorkSmallWindow : kHeavyWork;
+  P.part_work = o.window < kSmallWindow ? kPartWork : kPartWorkWide;
   P.time_limit_ns = time_limit_ns();
 
   // large windows take the wide grid (two blocks per SM)
@@ -601,6 +602,7 @@ int run_multi(const opmos_graph* g, uint32_t D, const opmos_options& o, const st
   P.qd = D;
   P.ps_grow = kMultiIndexGrow;
   P.heavy_work = kHeavyWork;
+  P.part_work = kPartWork;
   P.time_limit_ns = time_limit_ns();
   std::vector<MSlot> hslots(slots);
   for (unsigned i = 0; i < slots; ++i) {
@@ -1249,6 +1251,7 @@ int opmos_server_create(const opmos_graph* const* graphs, uint32_t ngraphs, cons
       sl.P.qd = sv->dmax;
       sl.P.ps_grow = kMultiIndexGrow;
       sl.P.heavy_work = kHeavyWork;
+      sl.P.part_work = kPartWork;
       sl.P.time_limit_ns = time_limit_ns();
       sl.state = SL_FREE;
     }

@@ -45,10 +45,12 @@ constexpr unsigned kHeavyWorkSmallWindow = 512;
 constexpr unsigned kHeavyWork = 2048;
 constexpr unsigned kSmallWindow = 16384;
 constexpr unsigned kHeavyCands = 32;      // ... and so are nodes reached by more candidates in a step
-// A block merge whose candidates x frontier entries exceed kPartWork is split
-// into parts (up to kPartsMax, each a whole block), each part holding at
-// least kPartCands candidates when the candidates are split.
-constexpr unsigned long long kPartWork = 1ull << 18;
+// A block merge whose candidates x frontier entries exceed the part work is
+// split into parts (up to kPartsMax, each a whole block), each part holding
+// at least kPartCands candidates when the candidates are split; the part
+// work is larger on the wide grid, whose blocks are three to an SM.
+constexpr unsigned kPartWork = 1u << 17;
+constexpr unsigned kPartWorkWide = 1u << 18;
 constexpr unsigned kPartsMax = 16;
 constexpr unsigned kPartCands = 64;
 constexpr unsigned kPartPruned = 1u << 16;  // added to a node's part counter by a part that pruned
@@ -250,6 +252,7 @@ struct QParams {
   uint32_t qd;            // objectives the query uses (<= the kernel's D; the rest read as 0)
   uint32_t ps_grow;       // the P index is rebuilt once the log outgrows it by 32 + count >> ps_grow
   uint32_t heavy_work;    // candidates x frontier entries from which a node is merged by a whole block
+  uint32_t part_work;     // ... per part of a split block merge
   unsigned long long time_limit_ns;
 };
 

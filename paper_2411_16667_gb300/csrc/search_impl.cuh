@@ -434,11 +434,11 @@ struct Search {
   }
 
   // Parts a block merge of nc candidates against F frontier entries is split
-  // into: a power of two, each part about kPartWork comparisons or fewer.
+  // into: a power of two, each part about P.part_work comparisons or fewer.
   __device__ unsigned parts_for(unsigned nc, unsigned F) const {
     const unsigned long long w = (unsigned long long)nc * F;
     unsigned k = 1;
-    while (k < A.kparts && w > kPartWork * k) k <<= 1;
+    while (k < A.kparts && w > (unsigned long long)P.part_work * k) k <<= 1;
     return k;
   }
 

@@ -208,6 +208,7 @@ int merge_hook(uint32_t nfront, const uint32_t* front, uint32_t ncand, const uin
   P.qd = D;
   P.ps_grow = 6;
   P.heavy_work = kHeavyWork;
+  P.part_work = kPartWork;
   OutPool O{nullptr, 0, nullptr};
   merge_hook_kernel<D><<<1, kGridThreads>>>(G, A, C, P, O, nfront, block);
   e = cudaGetLastError();
@@ -411,6 +412,7 @@ int opmos_test_window(uint32_t n, const uint32_t* f0, const uint32_t* f1, const 
     P.qd = D;
     P.ps_grow = 6;
     P.heavy_work = kHeavyWork;
+    P.part_work = kPartWork;
     const BinParams bp{bins[0], bins[1], bins[2], bins[3], bins[4]};
     OutPool O{nullptr, 0, nullptr};
     window_hist_kernel<<<64, 256>>>(A, n, bp, A.hist + 1 * kNB);
