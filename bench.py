@@ -71,8 +71,8 @@ CPU_SAMPLE_LABELS = 1_500_000
 # among them) they were taken with: a launch whose digest has no entry (the
 # sources changed, or another window was chosen) reports null.
 TRAFFIC = {
-    "5bd621afcd62ae48": 4094338816 + 2391912192,  # W = 262144
-    "4ffc5a29f6d3edc1": 1038509568 + 1080431360,  # W = 65536
+    "38885eb7713e8dda": 6056506368 + 4163967744,  # W = 262144
+    "f531d20f7e3bf6f6": 2690552832 + 2364830464,  # W = 65536
 }
 
 
