@@ -126,7 +126,7 @@ __device__ inline unsigned block_exclusive_scan(unsigned x, unsigned* s_warp, un
 constexpr unsigned kHC = 256;  // candidates a block merge holds at once
 
 struct Shared {
-  unsigned hist[kNB];  // this block's share of the next OPEN's histogram
+  alignas(16) unsigned hist[kNB];  // this block's share of the next OPEN's histogram
   unsigned warp[33];
   unsigned f_min, b1_max, bstar;
   unsigned pmax[3];
@@ -327,17 +327,25 @@ struct Search {
     constexpr unsigned kPer = kNB / 256;  // bins per thread: blocks have 256 threads or more
     static_assert(kGridThreads >= 256 && kGridWideThreads >= 256 && kMultiThreads >= 256, "kPer");
     const unsigned per = (kNB + blockDim.x - 1) / blockDim.x;
+    // the histogram (other SMs added to it: read past L1) staged in shared
+    // memory with 16-byte loads, then each thread takes `per` consecutive bins
+    {
+      const uint4* g4 = reinterpret_cast<const uint4*>(gh);
+      uint4* s4 = reinterpret_cast<uint4*>(S.hist);
+      for (unsigned x = threadIdx.x; x < kNB / 4; x += blockDim.x) s4[x] = __ldcg(g4 + x);
+    }
+    if (threadIdx.x == 0) {
+      S.f_min = kNB;
+      S.b1_max = 0;
+    }
+    __syncthreads();
     const unsigned b0 = threadIdx.x * per;
     unsigned loc[kPer];
     unsigned sum = 0;
 #pragma unroll
     for (unsigned j = 0; j < kPer; ++j) {
-      loc[j] = (j < per && b0 + j < (unsigned)kNB) ? ld_volatile(&gh[b0 + j]) : 0u;
+      loc[j] = (j < per && b0 + j < (unsigned)kNB) ? S.hist[b0 + j] : 0u;
       sum += loc[j];
-    }
-    if (threadIdx.x == 0) {
-      S.f_min = kNB;
-      S.b1_max = 0;
     }
     unsigned total;
     unsigned run = block_exclusive_scan(sum, S.warp, total);
@@ -359,6 +367,8 @@ struct Search {
     if (any_b1) atomicMax(&S.b1_max, b1);
     __syncthreads();
     if (threadIdx.x == 0) S.bstar = max(S.b1_max, S.f_min == (unsigned)kNB ? 0u : S.f_min);
+    // S.hist starts the next OPEN's histogram empty
+    for (unsigned x = threadIdx.x; x < kNB; x += blockDim.x) S.hist[x] = 0;
     __syncthreads();
   }
 
@@ -1877,7 +1887,6 @@ struct Search {
     const BinLimits bl = C->bins[r0];
     const BinParams bp{bl.b0, bl.b1, bl.s1, bl.delta, bl.s2};  // bins OPEN_i's histogram was built on
     bpn = next_bins(K0);
-    for (unsigned x = threadIdx.x; x < kNB; x += blockDim.x) S.hist[x] = 0;
     if (threadIdx.x == 0) {
       for (int j = 0; j < 5; ++j) S.tmax[j] = 0;
       const volatile PIdx* src = &C->pidx[cur];

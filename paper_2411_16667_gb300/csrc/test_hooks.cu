@@ -253,11 +253,9 @@ __global__ void __launch_bounds__(kGridThreads, 1) window_hook_kernel(GraphDev G
   X.psnap = 0;
   X.lbase = n;
   X.bpn = bp;
-  if (threadIdx.x == 0) {
-    S.pd = PIdx{};
-    for (int i = 0; i < kNB; ++i) S.hist[i] = 0;
-  }
-  X.select_window(A.hist + 1 * kNB);
+  if (threadIdx.x == 0) S.pd = PIdx{};
+  __syncthreads();
+  X.select_window(A.hist + 1 * kNB);  // leaves S.hist empty for the extraction
   if (threadIdx.x == 0) *bstar = S.bstar;
   const unsigned nchunks = (n + kChunk - 1) / kChunk;
   for (unsigned c = threadIdx.x >> 5; c < nchunks; c += blockDim.x >> 5) X.extract_chunk(c, n, bp, C->cyc[2]);
