@@ -71,8 +71,8 @@ CPU_SAMPLE_LABELS = 1_500_000
 # among them) they were taken with: a launch whose digest has no entry (the
 # sources changed, or another window was chosen) reports null.
 TRAFFIC = {
-    "38885eb7713e8dda": 6056506368 + 4163967744,  # W = 262144
-    "f531d20f7e3bf6f6": 2690552832 + 2364830464,  # W = 65536
+    "9f5e1906fe4f9546": 6107364352 + 4165698048,  # W = 262144
+    "3e3b8a0668a540e4": 2727929600 + 2369065984,  # W = 65536
 }
 
 
