@@ -531,7 +531,7 @@ int solve_one(const opmos_graph* g, const opmos_heur* heur, uint32_t start, uint
   P.part_work = o.window < kSmallWindow ? kPartWork : kPartWorkWide;
   P.time_limit_ns = time_limit_ns();
 
-  // large windows take the wide grid (two blocks per SM)
+  // large windows take the wide grid (three 256-thread blocks per SM)
   const bool wide = o.window >= kSmallWindow;
   int occ = search_occupancy(D, wide);
   if (occ <= 0) return fail(OPMOS_ERR_CUDA, "search kernel cannot be resident");
