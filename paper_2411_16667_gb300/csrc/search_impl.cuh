@@ -9,7 +9,9 @@
 //
 //   merge (window i)     the candidates produced by expanding window i are
 //                        merged node by node, one warp per target node (a
-//                        whole block for a node with a large frontier):
+//                        whole block when candidates x frontier entries are
+//                        many, split into parts of one block each when they
+//                        are very many):
 //                        resolved against each other (in-batch dominance and
 //                        duplicates), against the node's frontier alpha(v')
 //                        (Algorithm 1: weakly dominated candidates are dropped,
@@ -38,8 +40,9 @@
 // entries and new labels), on bins fixed at the start of step i. Its F[0]
 // origin is a lower bound on every key OPEN_{i+1} can hold: with a consistent
 // heuristic a child's F is at least its parent's, so min F[0] over OPEN plus
-// the window in flight never decreases. The 8 lowest F[0] buckets are split
-// by F[1].
+// the window in flight never decreases. A bin holds 2^s2 consecutive cells
+// q * 256 + x, q the F[0] bucket and x the F[1] cell of a key, so that every
+// bin prefix is a lexicographic prefix of OPEN.
 //
 // Determinism: a label pruned in step j is still extractable in step j (its
 // ldead word records j, and extraction drops labels with ldead < i), equal
