@@ -211,8 +211,10 @@ OPMOS_API int opmos_solve(const opmos_graph* g, const opmos_heur* heur, uint32_t
  * batching: up to 192 queries run at once in their own arenas (each
  * mem_budget_bytes / 192), all advancing one search step per grid iteration,
  * and a finished query's slot is refilled from the queue at once. A query
- * that outgrows its slot's arena is re-run alone with the single-query
- * arena. out receives nq results (each may be NULL) and status[q] each
+ * that outgrows its slot's arena, or creates more than opt->alone_labels
+ * labels there, is re-run alone afterwards (the single-query arena and
+ * kernel, window opt->alone_window). out receives nq results (each may be
+ * NULL) and status[q] each
  * query's own return code; the call returns OPMOS_OK when the batch ran, even
  * if some queries failed. */
 OPMOS_API int opmos_solve_batch(const opmos_graph* g, uint32_t nq, const uint32_t* starts,
