@@ -71,8 +71,8 @@ CPU_SAMPLE_LABELS = 1_500_000
 # among them) they were taken with: a launch whose digest has no entry (the
 # sources changed, or another window was chosen) reports null.
 TRAFFIC = {
-    "9f5e1906fe4f9546": 6107364352 + 4165698048,  # W = 262144
-    "3e3b8a0668a540e4": 2727929600 + 2369065984,  # W = 65536
+    "7368f652d975998e": 6032931840 + 4144625152,  # W = 262144
+    "903b9a5f7ee557e5": 2759832064 + 2360845056,  # W = 65536
 }
 
 

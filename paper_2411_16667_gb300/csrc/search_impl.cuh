@@ -325,10 +325,18 @@ struct Search {
   // ---------------- window selection (Algorithm 2: NUM_POP lowest labels) ----------------
   // Bins [0, b*] where b* is the largest bin whose cumulative count is <= W,
   // but at least the first non-empty bin (the overflow bin is never taken).
-  // Every block computes the same b* into S.bstar.
-  __device__ void select_window(const unsigned* gh) {
+  // Every block computes the same b* into S.bstar. all: OPEN holds at most W
+  // entries, so every bin but the last has a cumulative count within W and
+  // b* is kNB - 2 without reading the histogram.
+  __device__ void select_window(const unsigned* gh, bool all = false) {
     constexpr unsigned kPer = kNB / 256;  // bins per thread: blocks have 256 threads or more
     static_assert(kGridThreads >= 256 && kGridWideThreads >= 256 && kMultiThreads >= 256, "kPer");
+    if (all) {
+      if (threadIdx.x == 0) S.bstar = kNB - 2;
+      for (unsigned x = threadIdx.x; x < kNB; x += blockDim.x) S.hist[x] = 0;
+      __syncthreads();
+      return;
+    }
     const unsigned per = (kNB + blockDim.x - 1) / blockDim.x;
     // the histogram (other SMs added to it: read past L1) staged in shared
     // memory with 16-byte loads, then each thread takes `per` consecutive bins
@@ -1902,7 +1910,7 @@ struct Search {
       S.pd.k = src->k;
       for (int j = 0; j < 3; ++j) S.pd.shift[j] = src->shift[j];
     }
-    select_window(A.hist + r0 * kNB);  // has block barriers: S.pd is visible after it
+    select_window(A.hist + r0 * kNB, n_in <= P.window);  // has block barriers: S.pd is visible after it
     for (unsigned x = T.tid(); x < kNB; x += T.nthreads()) A.hist[r2 * kNB + x] = 0;
     if (T.leader_block()) {
       if (threadIdx.x == 0) {
